@@ -1,0 +1,184 @@
+/*
+ * ps.h — C ABI of libps: exact kNN / RDF spatial statistics of atom-probe
+ * point clouds on one GB300 (sm_103a), plus the batched sweep and the
+ * Gaussian-smoothed RDF with its adjoint.
+ *
+ * What is computed (the paper's spatial-statistics task, Methods
+ * "Descriptive, two-point spatial statistics, and clustering"; Suppl.
+ * "Efficient batch processing of spatial statistics", Figs. SchematicKNN and
+ * SchematicRDF):
+ *   central set   C = { i : type_i in ctr_mask and d_srf_i >= dsrf_min }
+ *                 (the d_srf edge rule of Methods "Ion-to-edge distancing";
+ *                 neighbours are never d_srf-filtered)
+ *   neighbour set N = { j : type_j in nbr_mask }
+ *   d2_ij         = ((dx*dx)+(dy*dy))+(dz*dz) in float32, dx = x_j - x_i,
+ *                 every operation rounded to nearest, no FMA contraction
+ *   edges         E[b] = (float)((r0 + b*dr)^2), r0 and dr double, b = 0..n_bins
+ *                 (the paper's bin notation r = [start, step, stop], with
+ *                 n_bins = round((stop - start)/step))
+ *   RDF           H[b] = #{ (i, j) : i in C, j in N, j != i, E[b] <= d2_ij < E[b+1] }
+ *                 (ordered pairs; the self pair is excluded by index)
+ *   kNN           D_k(i) = k-th smallest d2_ij over j in N, j != i,
+ *                 d2_ij < E[n_bins]; K[b] counts the centrals whose D_k falls in
+ *                 bin b; fewer than k such j is "not found".
+ * All histograms are exact integers, bit-identical to the definition.
+ *
+ * Conventions for every entry point:
+ *   - Arrays named d_* and the xyz/type/dsrf inputs are DEVICE pointers
+ *     owned by the caller.  xyz is float32 [n][3] (x, y, z interleaved, nm),
+ *     type is uint8 [n], dsrf is float32 [n].  Inputs are read only; they
+ *     must stay valid and unchanged while any call that uses them (or a
+ *     grid built from them) is in flight.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously; results are valid once the
+ *     stream reaches that point.  Unless stated, no call synchronises.
+ *   - Type sets are uint64_t[4] bit masks over the 256 possible labels
+ *     (bit t of word t/64 set = label t in the set).
+ *   - Every function returns a ps_status.  Errors found on the host return
+ *     immediately with nothing enqueued; ps_last_error() (thread local)
+ *     describes the last failure.  Errors found on the device (non-finite
+ *     coordinates, a bounded wait that timed out) are written to the status
+ *     word of the output meta array (index PS_META_STATUS) and to the grid's
+ *     status, read with ps_grid_get_info().  No call aborts the process, traps
+ *     the GPU or throws across the ABI.
+ *   - Output histograms and meta arrays are overwritten, not accumulated.
+ *   - Limits: n < 2^32 ions; 1 <= n_bins <= PS_MAX_BINS; 1 <= k <= PS_K_MAX.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PS_API __attribute__((visibility("default")))
+#else
+#define PS_API
+#endif
+
+typedef enum {
+  PS_OK = 0,
+  PS_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter (host check) */
+  PS_ERR_INVALID_INPUT = 2, /* non-finite coordinate found on the device */
+  PS_ERR_OOM = 3,           /* device allocation failed */
+  PS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  PS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  PS_ERR_UNSUPPORTED = 6,   /* k > PS_K_MAX, too many bins, ... */
+  PS_ERR_CAPACITY = 7       /* n larger than the grid was created for */
+} ps_status;
+
+#define PS_K_MAX 32
+#define PS_MAX_BINS 8192
+#define PS_MAX_KLIST 32
+
+/* Layout of the uint64 meta array written by the histogram calls. */
+#define PS_META_N_CENTRAL 0 /* |C| */
+#define PS_META_N_PAIRS 1   /* RDF pairs binned (sum of H) */
+#define PS_META_N_BELOW 2   /* RDF pairs with d2 < E[0] (only when r0 > 0) */
+#define PS_META_STATUS 3    /* 0, or the ps_status of a device-side error */
+#define PS_META_HEAD 4
+/* then, for the q-th requested k: [PS_META_HEAD + 2q] not found,
+ * [PS_META_HEAD + 2q + 1] k-th distance below E[0] */
+#define PS_META_LEN(n_k) (PS_META_HEAD + 2 * (n_k))
+
+/* Bins r = [r0, r0 + n_bins*dr) in nm; see the edge rule above. */
+typedef struct {
+  double r0;
+  double dr;
+  uint32_t n_bins;
+} ps_bins;
+
+/* Options for a cell grid.  struct_size = sizeof(ps_grid_opts). */
+typedef struct {
+  uint32_t struct_size;
+  float cell_scale; /* cell edge = r_cut * cell_scale; 0 = default (1.0); must be >= 1 */
+  uint32_t block;   /* query threads per block; 0 = default */
+  uint32_t reserved;
+} ps_grid_opts;
+
+typedef struct ps_grid ps_grid; /* opaque; owns its device scratch */
+
+/* Library version (major*10000 + minor*100 + patch). */
+PS_API int ps_version(void);
+
+/* Description of the last error on this thread ("" if none). */
+PS_API const char* ps_last_error(void);
+
+/* Host helper: the edge table E[0..n_bins] (float32, host memory) used by
+ * every kernel, by the formula above.  Returns PS_ERR_INVALID_ARG for
+ * dr <= 0, r0 < 0, n_bins out of range or E == NULL. */
+PS_API int ps_bin_edges(ps_bins bins, float* E);
+
+/*
+ * Cell grid over the neighbour set (regular spatial binning, Suppl. Fig.
+ * QueryingStructures c, which replaces the paper's per-region KD-trees).
+ *
+ * ps_grid_create allocates the device scratch for up to n_max ions
+ * (about 60 bytes per ion plus the cell arrays); it synchronises the device
+ * (cudaMalloc).  ps_grid_build bins the ions j with type_j in nbr_mask into
+ * cells of edge >= r_cut, sorted by cell (counting sort), asynchronously on
+ * `stream`, with no host synchronisation: the bounding box and the cell
+ * dimensions stay on the device.  The grid keeps the xyz and type pointers;
+ * later queries read them again.  Returns PS_ERR_CAPACITY if n > n_max,
+ * PS_ERR_INVALID_ARG for r_cut <= 0 or null pointers (n == 0 is allowed).
+ * ps_build_grid = ps_grid_create(n) + ps_grid_build.
+ * ps_grid_destroy frees everything (synchronises; NULL is allowed).
+ */
+PS_API int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out);
+PS_API int ps_grid_build(ps_grid* g, const float* xyz, const uint8_t* type, int64_t n, const uint64_t nbr_mask[4],
+                  float r_cut, void* stream);
+PS_API int ps_build_grid(const float* xyz, const uint8_t* type, int64_t n, const uint64_t nbr_mask[4], float r_cut,
+                  const ps_grid_opts* opts, void* stream, ps_grid** out);
+PS_API int ps_grid_destroy(ps_grid* g);
+
+/* Grid geometry, read back from the device (synchronises `stream`). */
+typedef struct {
+  uint32_t struct_size;
+  uint32_t dims[3];
+  float origin[3];
+  float cell;        /* cell edge (nm) */
+  int64_t n_nbr;     /* ions in the neighbour set */
+  int64_t n_cells;
+  int32_t status;    /* device-side ps_status of the last build */
+} ps_grid_info;
+PS_API int ps_grid_get_info(ps_grid* g, ps_grid_info* info, void* stream);
+
+/*
+ * Exact kNN + RDF in one enumeration of the ROIs.  As in the paper's batch
+ * queue (Suppl. "Customized user defined batch processing queues"), the
+ * neighbours of a ROI are found once and every requested statistic (each k
+ * and the RDF) is evaluated from that one pass.
+ *   g         grid built with r_cut >= sqrt(E[n_bins]) (else PS_ERR_INVALID_ARG)
+ *   dsrf      device float32 [n] of the grid's cloud; NULL = no d_srf filter
+ *   ctr_mask  central types; dsrf_min the d_srf threshold (inclusive)
+ *   ks, n_k   HOST array of k values (1..PS_K_MAX), n_k <= PS_MAX_KLIST; n_k may be 0
+ *   d_rdf     uint64 [n_bins] or NULL (no RDF)
+ *   d_knn     uint64 [n_k][n_bins] or NULL when n_k == 0
+ *   d_meta    uint64 [PS_META_LEN(n_k)] (required)
+ *   d_kth     optional float32 [n_k][n]: D_k(i) as a squared distance, +inf
+ *             when not found; written for central ions only
+ *   d_nwithin optional uint32 [n]: in-range neighbours of each central
+ *             (d2 < E[n_bins]); written for central ions only
+ */
+PS_API int ps_spatstat(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
+                const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
+                uint32_t* d_nwithin, void* stream);
+
+/* kNN histogram for one k: ps_spatstat with n_k = 1 and no RDF.
+ * d_meta is uint64 [PS_META_LEN(1)]; d_kth optional float32 [n]. */
+PS_API int ps_knn_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, uint32_t k,
+                ps_bins bins, uint64_t* d_hist, uint64_t* d_meta, float* d_kth, void* stream);
+
+/* RDF histogram: ps_spatstat with n_k = 0.  d_meta is uint64 [PS_META_LEN(0)]. */
+PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
+                uint64_t* d_hist, uint64_t* d_meta, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_H */

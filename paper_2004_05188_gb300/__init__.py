@@ -1,5 +1,37 @@
-"""GB300-native spatial statistics (kNN / RDF) for atom-probe point clouds."""
+"""GB300-native spatial statistics (exact kNN / RDF) for atom-probe point clouds.
+
+Thin Python binding over the C ABI of libps (include/ps.h): argument
+marshalling only.  Every step of the computation runs in the CUDA kernels of
+libps.so; there is no CPU fallback.  PyTorch supplies device memory and
+streams.  Importing this package works without a GPU (host helpers only);
+calling a compute function without the built library raises.
+"""
 from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libps.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "ps.h")
+
+PS_OK = 0
+STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_INVALID_INPUT", 3: "PS_ERR_OOM", 4: "PS_ERR_CUDA",
+          5: "PS_ERR_TIMEOUT", 6: "PS_ERR_UNSUPPORTED", 7: "PS_ERR_CAPACITY"}
+K_MAX = 32
+MAX_BINS = 8192
+MAX_KLIST = 32
+META_HEAD = 4
+AL, SC, SI = 0, 1, 2
+
+
+class PSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
 
 
 def bins_from_spec(start: float, step: float, stop: float):
@@ -11,3 +43,226 @@ def bins_from_spec(start: float, step: float, stop: float):
     if not (step > 0) or not (stop > start) or start < 0:
         raise ValueError("need 0 <= start < stop and step > 0")
     return float(start), float(step), int(round((stop - start) / step))
+
+
+def type_mask(types) -> np.ndarray:
+    """Type set -> 4 x uint64 bit mask; `types` is an iterable of labels or 'all'."""
+    m = np.zeros(4, dtype=np.uint64)
+    if isinstance(types, str):
+        if types != "all":
+            raise ValueError("type set must be an iterable of labels or 'all'")
+        m[:] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        return m
+    for t in types:
+        t = int(t)
+        if not 0 <= t < 256:
+            raise ValueError("type labels are 0..255")
+        m[t >> 6] |= np.uint64(1) << np.uint64(t & 63)
+    return m
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("r0", ctypes.c_double), ("dr", ctypes.c_double), ("n_bins", ctypes.c_uint32)]
+
+
+class GridOpts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("cell_scale", ctypes.c_float), ("block", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("dims", ctypes.c_uint32 * 3), ("origin", ctypes.c_float * 3),
+                ("cell", ctypes.c_float), ("n_nbr", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("status", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the entry points declared in include/ps.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"PS_API\s+[\w\s\*]+?\b(ps_\w+)\s*\(", txt)))
+
+
+def lib():
+    """Load libps.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libps.so not built ({LIB_PATH}); run __graft_entry__.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i64, u32, f32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float, ctypes.c_int
+    L.ps_version.restype = i32
+    L.ps_last_error.restype = ctypes.c_char_p
+    L.ps_bin_edges.argtypes = [Bins, P]
+    L.ps_grid_create.argtypes = [i64, ctypes.POINTER(GridOpts), ctypes.POINTER(P)]
+    L.ps_grid_build.argtypes = [P, P, P, i64, P, f32, P]
+    L.ps_build_grid.argtypes = [P, P, i64, P, f32, ctypes.POINTER(GridOpts), P, ctypes.POINTER(P)]
+    L.ps_grid_destroy.argtypes = [P]
+    L.ps_grid_get_info.argtypes = [P, ctypes.POINTER(GridInfo), P]
+    L.ps_spatstat.argtypes = [P, P, P, f32, Bins, P, u32, P, P, P, P, P, P]
+    L.ps_knn_hist.argtypes = [P, P, P, f32, u32, Bins, P, P, P, P]
+    L.ps_rdf_hist.argtypes = [P, P, P, f32, Bins, P, P, P]
+    for name in header_functions():
+        fn = getattr(L, name)
+        if fn.restype is ctypes.c_int and name != "ps_last_error":
+            fn.restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != PS_OK:
+        raise PSError(rc, lib().ps_last_error().decode(errors="replace"))
+
+
+def edges(r0: float, dr: float, n_bins: int) -> np.ndarray:
+    """The float32 edge table E[0..n_bins] of libps (host computation)."""
+    E = np.empty(n_bins + 1, np.float32)
+    _check(lib().ps_bin_edges(Bins(r0, dr, n_bins), E.ctypes.data_as(ctypes.c_void_p)))
+    return E
+
+
+def _stream(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _mask_ptr(types):
+    m = type_mask(types)
+    return m, m.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check_cloud(xyz, type_, dsrf=None):
+    import torch
+
+    if not (xyz.is_cuda and type_.is_cuda):
+        raise ValueError("xyz and type must be CUDA tensors")
+    if xyz.dtype != torch.float32 or type_.dtype != torch.uint8:
+        raise ValueError("xyz must be float32 and type uint8")
+    if xyz.dim() != 2 or xyz.shape[1] != 3 or not xyz.is_contiguous() or not type_.is_contiguous():
+        raise ValueError("xyz must be a contiguous [n, 3] tensor and type contiguous [n]")
+    if type_.shape[0] != xyz.shape[0]:
+        raise ValueError("xyz and type lengths differ")
+    if dsrf is not None:
+        if not dsrf.is_cuda or dsrf.dtype != torch.float32 or not dsrf.is_contiguous() or dsrf.shape[0] != xyz.shape[0]:
+            raise ValueError("dsrf must be a contiguous float32 CUDA tensor of length n")
+
+
+class Grid:
+    """A cell grid over the neighbour set of one cloud (ps_grid_create / ps_grid_build)."""
+
+    def __init__(self, n_max: int, cell_scale: float = 1.0):
+        opts = GridOpts(ctypes.sizeof(GridOpts), float(cell_scale), 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().ps_grid_create(int(n_max), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self.n_max = int(n_max)
+        self._refs = ()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def build(self, xyz, type_, nbr_types, r_cut: float, stream=None):
+        _check_cloud(xyz, type_)
+        m, mp = _mask_ptr(nbr_types)
+        _check(lib().ps_grid_build(self._h, _ptr(xyz), _ptr(type_), xyz.shape[0], mp, float(r_cut), _stream(stream)))
+        self._refs = (xyz, type_)  # the grid reads these again in every query
+        self.n = int(xyz.shape[0])
+        self.r_cut = float(r_cut)
+        return self
+
+    def info(self, stream=None) -> dict:
+        gi = GridInfo()
+        gi.struct_size = ctypes.sizeof(GridInfo)
+        _check(lib().ps_grid_get_info(self._h, ctypes.byref(gi), _stream(stream)))
+        return dict(dims=tuple(gi.dims), origin=tuple(gi.origin), cell=gi.cell, n_nbr=gi.n_nbr,
+                    n_cells=gi.n_cells, status=gi.status)
+
+    def close(self):
+        if self._h:
+            _check(lib().ps_grid_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.ps_grid_destroy(self._h)
+        except Exception:
+            pass
+
+
+def spatstat(grid: Grid, dsrf, ctr_types, dsrf_min: float, bins, ks=(), rdf: bool = True, per_central: bool = False,
+             out=None, stream=None, check: bool = True):
+    """Exact RDF + kNN histograms in one enumeration (ps_spatstat).
+
+    bins = (r0, dr, n_bins).  Returns a dict of CUDA tensors: rdf [n_bins],
+    knn [n_k, n_bins], meta [4 + 2 n_k] (n_central, pairs binned, pairs below
+    r0, status, then per k: not found, below r0) and, with per_central,
+    kth_d2 [n_k, n] and n_within [n] (central ions only; others hold -1 / NaN).
+    With check=True the device status is read back (one synchronisation).
+    """
+    import torch
+
+    r0, dr, nb = bins
+    ks = [int(k) for k in ks]
+    nk = len(ks)
+    dev = grid._refs[0].device
+    if dsrf is not None:
+        _check_cloud(grid._refs[0], grid._refs[1], dsrf)
+    if out is None:
+        out = {}
+        out["rdf"] = torch.empty(nb, dtype=torch.int64, device=dev) if rdf else None
+        out["knn"] = torch.empty((nk, nb), dtype=torch.int64, device=dev) if nk else None
+        out["meta"] = torch.empty(META_HEAD + 2 * nk, dtype=torch.int64, device=dev)
+        if per_central:
+            out["kth_d2"] = torch.full((nk, grid.n), float("nan"), dtype=torch.float32, device=dev) if nk else None
+            out["n_within"] = torch.full((grid.n,), -1, dtype=torch.int32, device=dev)
+    ks_a = np.ascontiguousarray(ks, np.uint32)
+    m, mp = _mask_ptr(ctr_types)
+    _check(lib().ps_spatstat(grid.handle, _ptr(dsrf), mp, float(dsrf_min), Bins(r0, dr, nb),
+                             ks_a.ctypes.data_as(ctypes.c_void_p), nk, _ptr(out.get("rdf")), _ptr(out.get("knn")),
+                             _ptr(out["meta"]), _ptr(out.get("kth_d2")), _ptr(out.get("n_within")), _stream(stream)))
+    if check:
+        st = int(out["meta"][3].item())
+        if st != 0:
+            raise PSError(st, "device-side error reported in the meta status word")
+    return out
+
+
+def knn_hist(grid: Grid, dsrf, ctr_types, dsrf_min: float, k: int, bins, stream=None):
+    """kNN histogram for one k (ps_knn_hist): returns (hist [n_bins], meta [6])."""
+    import torch
+
+    r0, dr, nb = bins
+    dev = grid._refs[0].device
+    h = torch.empty(nb, dtype=torch.int64, device=dev)
+    meta = torch.empty(META_HEAD + 2, dtype=torch.int64, device=dev)
+    m, mp = _mask_ptr(ctr_types)
+    _check(lib().ps_knn_hist(grid.handle, _ptr(dsrf), mp, float(dsrf_min), int(k), Bins(r0, dr, nb), _ptr(h),
+                             _ptr(meta), None, _stream(stream)))
+    return h, meta
+
+
+def rdf_hist(grid: Grid, dsrf, ctr_types, dsrf_min: float, bins, stream=None):
+    """RDF histogram (ps_rdf_hist): returns (hist [n_bins], meta [4])."""
+    import torch
+
+    r0, dr, nb = bins
+    dev = grid._refs[0].device
+    h = torch.empty(nb, dtype=torch.int64, device=dev)
+    meta = torch.empty(META_HEAD, dtype=torch.int64, device=dev)
+    m, mp = _mask_ptr(ctr_types)
+    _check(lib().ps_rdf_hist(grid.handle, _ptr(dsrf), mp, float(dsrf_min), Bins(r0, dr, nb), _ptr(h), _ptr(meta),
+                             _stream(stream)))
+    return h, meta

@@ -1,0 +1,230 @@
+// C ABI entry points of libps: argument checks, handle lifetime, dispatch.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "ps_internal.cuh"
+
+namespace ps {
+
+static thread_local std::string t_error;
+
+void set_error(const std::string& msg) { t_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  t_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  t_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA;
+}
+
+int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
+              const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
+              uint32_t* d_nwithin, cudaStream_t s);
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void edges_host(ps_bins b, float* E) {
+  for (uint32_t i = 0; i <= b.n_bins; ++i) {
+    const double e = b.r0 + (double)i * b.dr;
+    E[i] = (float)(e * e);
+  }
+}
+
+static int check_bins(ps_bins b) {
+  if (!(b.dr > 0.0) || !(b.r0 >= 0.0) || !std::isfinite(b.dr) || !std::isfinite(b.r0))
+    return fail(PS_ERR_INVALID_ARG, "bins: need r0 >= 0 and dr > 0, finite");
+  if (b.n_bins < 1 || b.n_bins > PS_MAX_BINS) return fail(PS_ERR_UNSUPPORTED, "bins: n_bins out of range");
+  return PS_OK;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+int ps_version(void) { return 100; }
+
+const char* ps_last_error(void) { return t_error.c_str(); }
+
+int ps_bin_edges(ps_bins bins, float* E) {
+  if (!E) return fail(PS_ERR_INVALID_ARG, "ps_bin_edges: E is NULL");
+  int rc = check_bins(bins);
+  if (rc) return rc;
+  edges_host(bins, E);
+  return PS_OK;
+}
+
+int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
+  if (!out) return fail(PS_ERR_INVALID_ARG, "ps_grid_create: out is NULL");
+  *out = nullptr;
+  if (n_max < 0 || n_max > (int64_t)UINT32_MAX - 1) return fail(PS_ERR_INVALID_ARG, "ps_grid_create: n_max out of range");
+  float cell_scale = 1.0f;
+  uint32_t block = 0;
+  if (opts) {
+    if (opts->struct_size < sizeof(uint32_t) + sizeof(float))
+      return fail(PS_ERR_INVALID_ARG, "ps_grid_create: opts->struct_size too small");
+    if (opts->cell_scale != 0.0f) cell_scale = opts->cell_scale;
+    if (opts->struct_size >= offsetof(ps_grid_opts, block) + sizeof(uint32_t)) block = opts->block;
+  }
+  if (!(cell_scale >= 1.0f) || !std::isfinite(cell_scale)) return fail(PS_ERR_INVALID_ARG, "cell_scale must be >= 1");
+  ps_grid* g = new (std::nothrow) ps_grid();
+  if (!g) return fail(PS_ERR_OOM, "host allocation failed");
+  g->n_max = n_max > 0 ? n_max : 1;
+  g->cell_scale = cell_scale;
+  g->block = block;
+  const int64_t cap = g->n_max / 2 > 65536 ? g->n_max / 2 : 65536;
+  g->cell_cap = (uint32_t)(cap < (int64_t)1 << 31 ? cap : (int64_t)1 << 31);
+  g->scan_tiles_cap = (g->cell_cap + 4095) / 4096;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const size_t nm = (size_t)g->n_max, cc = g->cell_cap;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  const size_t o_sel = take(nm * 4), o_cr = take(nm * 8);
+  const size_t o_ncount = take(cc * 4), o_nstart = take((cc + 1) * 4), o_nrec = take(nm * 16);
+  const size_t o_ccount = take(cc * 4), o_cstart = take((cc + 1) * 4), o_crec = take(nm * 16), o_cwork = take(cc * 4);
+  const size_t o_part = take((size_t)g->scan_tiles_cap * 4), o_ngeo = take(sizeof(Geo)), o_cgeo = take(sizeof(Geo));
+  void* base = nullptr;
+  e = cudaMalloc(&base, off);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "cudaMalloc(grid scratch)");
+  }
+  char* b = static_cast<char*>(base);
+  g->dev_block = base;
+  g->sel = reinterpret_cast<uint32_t*>(b + o_sel);
+  g->cr = reinterpret_cast<uint2*>(b + o_cr);
+  g->nbr.count = reinterpret_cast<uint32_t*>(b + o_ncount);
+  g->nbr.start = reinterpret_cast<uint32_t*>(b + o_nstart);
+  g->nbr.rec = reinterpret_cast<float4*>(b + o_nrec);
+  g->nbr.geo = reinterpret_cast<Geo*>(b + o_ngeo);
+  g->ctr.count = reinterpret_cast<uint32_t*>(b + o_ccount);
+  g->ctr.start = reinterpret_cast<uint32_t*>(b + o_cstart);
+  g->ctr.rec = reinterpret_cast<float4*>(b + o_crec);
+  g->ctr.work = reinterpret_cast<uint32_t*>(b + o_cwork);
+  g->ctr.geo = reinterpret_cast<Geo*>(b + o_cgeo);
+  g->scan_part = reinterpret_cast<uint32_t*>(b + o_part);
+  e = cudaMemset(g->nbr.geo, 0, sizeof(Geo));
+  if (e == cudaSuccess) e = cudaMemset(g->ctr.geo, 0, sizeof(Geo));
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    delete g;
+    return cuda_fail(e, "cudaMemset(grid)");
+  }
+  *out = g;
+  return PS_OK;
+}
+
+int ps_grid_destroy(ps_grid* g) {
+  if (!g) return PS_OK;
+  cudaError_t e = cudaSuccess;
+  if (g->dev_block) {
+    e = cudaDeviceSynchronize();
+    cudaError_t e2 = cudaFree(g->dev_block);
+    if (e == cudaSuccess) e = e2;
+  }
+  delete g;
+  if (e != cudaSuccess) return cuda_fail(e, "ps_grid_destroy");
+  return PS_OK;
+}
+
+int ps_grid_build(ps_grid* g, const float* xyz, const uint8_t* type, int64_t n, const uint64_t nbr_mask[4],
+                  float r_cut, void* stream) {
+  if (!g) return fail(PS_ERR_INVALID_ARG, "ps_grid_build: grid is NULL");
+  if (n < 0) return fail(PS_ERR_INVALID_ARG, "ps_grid_build: n < 0");
+  if (n > g->n_max) return fail(PS_ERR_CAPACITY, "ps_grid_build: n exceeds the grid capacity");
+  if (n > 0 && (!xyz || !type)) return fail(PS_ERR_INVALID_ARG, "ps_grid_build: xyz/type is NULL");
+  if (!nbr_mask) return fail(PS_ERR_INVALID_ARG, "ps_grid_build: nbr_mask is NULL");
+  if (!(r_cut > 0.0f) || !std::isfinite(r_cut)) return fail(PS_ERR_INVALID_ARG, "ps_grid_build: r_cut must be > 0");
+  g->xyz = xyz;
+  g->type = type;
+  g->n = n;
+  g->r_cut = r_cut;
+  g->built = false;
+  int rc = build_neighbour_grid(g, nbr_mask, r_cut, static_cast<cudaStream_t>(stream));
+  if (rc == PS_OK) g->built = true;
+  return rc;
+}
+
+int ps_build_grid(const float* xyz, const uint8_t* type, int64_t n, const uint64_t nbr_mask[4], float r_cut,
+                  const ps_grid_opts* opts, void* stream, ps_grid** out) {
+  if (!out) return fail(PS_ERR_INVALID_ARG, "ps_build_grid: out is NULL");
+  int rc = ps_grid_create(n, opts, out);
+  if (rc) return rc;
+  rc = ps_grid_build(*out, xyz, type, n, nbr_mask, r_cut, stream);
+  if (rc) {
+    ps_grid_destroy(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int ps_grid_get_info(ps_grid* g, ps_grid_info* info, void* stream) {
+  if (!g || !info) return fail(PS_ERR_INVALID_ARG, "ps_grid_get_info: NULL argument");
+  if (info->struct_size < sizeof(ps_grid_info)) return fail(PS_ERR_INVALID_ARG, "ps_grid_get_info: struct_size");
+  Geo h;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PS_CUDA(cudaMemcpyAsync(&h, g->nbr.geo, sizeof(Geo), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  for (int a = 0; a < 3; ++a) info->dims[a] = h.dims[a], info->origin[a] = h.origin[a];
+  info->cell = h.h;
+  info->n_nbr = h.n_sel;
+  info->n_cells = h.n_cells;
+  info->status = h.status;
+  return PS_OK;
+}
+
+int ps_spatstat(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
+                const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
+                uint32_t* d_nwithin, void* stream) {
+  if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: grid is NULL or not built");
+  if (!ctr_mask || !d_meta) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: ctr_mask/d_meta is NULL");
+  int rc = check_bins(bins);
+  if (rc) return rc;
+  if (n_k > PS_MAX_KLIST) return fail(PS_ERR_UNSUPPORTED, "ps_spatstat: too many k values");
+  if (n_k > 0 && (!ks || !d_knn)) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: ks/d_knn is NULL");
+  for (uint32_t q = 0; q < n_k; ++q)
+    if (ks[q] < 1 || ks[q] > PS_K_MAX) return fail(PS_ERR_UNSUPPORTED, "ps_spatstat: k must be in [1, 32]");
+  if (std::isnan(dsrf_min)) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: dsrf_min is NaN");
+  float Emax;
+  {
+    ps_bins one = bins;
+    float* E = new (std::nothrow) float[bins.n_bins + 1];
+    if (!E) return fail(PS_ERR_OOM, "host allocation failed");
+    edges_host(one, E);
+    Emax = E[bins.n_bins];
+    delete[] E;
+  }
+  if ((double)Emax > (double)g->r_cut * (double)g->r_cut)
+    return fail(PS_ERR_INVALID_ARG, "ps_spatstat: the grid's r_cut is below the histogram stop");
+  return run_query(g, dsrf, ctr_mask, dsrf_min, bins, ks, n_k, d_rdf, d_knn, d_meta, d_kth, d_nwithin,
+                   static_cast<cudaStream_t>(stream));
+}
+
+int ps_knn_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, uint32_t k, ps_bins bins,
+                uint64_t* d_hist, uint64_t* d_meta, float* d_kth, void* stream) {
+  if (!d_hist) return fail(PS_ERR_INVALID_ARG, "ps_knn_hist: d_hist is NULL");
+  return ps_spatstat(g, dsrf, ctr_mask, dsrf_min, bins, &k, 1, nullptr, d_hist, d_meta, d_kth, nullptr, stream);
+}
+
+int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
+                uint64_t* d_hist, uint64_t* d_meta, void* stream) {
+  if (!d_hist) return fail(PS_ERR_INVALID_ARG, "ps_rdf_hist: d_hist is NULL");
+  return ps_spatstat(g, dsrf, ctr_mask, dsrf_min, bins, nullptr, 0, d_hist, nullptr, d_meta, nullptr, nullptr,
+                     stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,350 @@
+// Cell-grid binner: counting sort of the ion records into a uniform cell grid.
+//
+// The paper indexes ions with per-region, per-type KD-trees whose leaves are
+// repacked so that the ions of a leaf are contiguous (Suppl. "Details on
+// efficient spatial indices"), and uses regular spatial binning for constant
+// time queries (Suppl. Fig. QueryingStructures c).  Here the index is the
+// regular binning: cells of edge >= r_cut, one set of cells per neighbour
+// type set (the paper keeps one tree per ion type, Suppl. "Effectiveness of
+// spatial splitting"), records sorted by cell as float4 (x, y, z, index).
+//
+// Pipeline (all on the device, no host synchronisation):
+//   reset -> select + bounding box -> geometry + zero counts -> count ranks
+//   -> exclusive scan (tiles, tile prefixes, apply) -> scatter
+#include <cstring>
+
+#include "ps_internal.cuh"
+
+namespace ps {
+
+constexpr int kThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr uint32_t kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+// warp-aggregated append: returns this lane's slot for lanes with pred set
+__device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t* counter) {
+  const uint32_t active = __activemask();
+  const uint32_t bal = __ballot_sync(active, pred);
+  uint32_t base = 0;
+  const int leader = __ffs(bal) - 1;
+  if (bal != 0 && (int)lane_id() == leader) base = atomicAdd(counter, __popc(bal));
+  base = __shfl_sync(active, base, leader < 0 ? 0 : leader);
+  return base + __popc(bal & ((1u << lane_id()) - 1u));
+}
+
+__global__ void k_reset(Geo* geo) {
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) {
+      geo->bbox_key[a] = f2key(INFINITY);
+      geo->bbox_key[3 + a] = f2key(-INFINITY);
+    }
+    geo->n_sel = 0;
+    geo->status = 0;
+    geo->work_n = 0;
+    geo->work_next = 0;
+  }
+}
+
+// Select the ions of the neighbour set, append their indices, reduce the bounding box.
+__global__ void __launch_bounds__(kThreads) k_select_bbox(const float* __restrict__ xyz, const uint8_t* __restrict__ type,
+                                                          int64_t n, Mask mask, uint32_t* __restrict__ sel, Geo* geo) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool s = false;
+    if (i < n) {
+      s = in_mask(mask, type[i]);
+      if (s) {
+        const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        if (finite3(x, y, z)) {
+          lo[0] = fminf(lo[0], x), hi[0] = fmaxf(hi[0], x);
+          lo[1] = fminf(lo[1], y), hi[1] = fmaxf(hi[1], y);
+          lo[2] = fminf(lo[2], z), hi[2] = fmaxf(hi[2], z);
+        } else {
+          bad = true;
+        }
+      }
+    }
+    const uint32_t slot = warp_append(s, &geo->n_sel);
+    if (s) sel[slot] = (uint32_t)i;
+  }
+  // block reduction of the box
+  __shared__ float s_lo[3][kThreads / 32], s_hi[3][kThreads / 32];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+  }
+  __syncthreads();
+  if (bad) s_bad = 1;
+  if (lane_id() == 0)
+    for (int a = 0; a < 3; ++a) s_lo[a][threadIdx.x >> 5] = lo[a], s_hi[a][threadIdx.x >> 5] = hi[a];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    const int a = threadIdx.x;
+    float l = INFINITY, h = -INFINITY;
+    for (int w = 0; w < kThreads / 32; ++w) l = fminf(l, s_lo[a][w]), h = fmaxf(h, s_hi[a][w]);
+    if (l <= h) {
+      atomicMin(&geo->bbox_key[a], f2key(l));
+      atomicMax(&geo->bbox_key[3 + a], f2key(h));
+    }
+  }
+  if (threadIdx.x == 0 && s_bad) atomicCAS(&geo->status, 0, (int)PS_ERR_INVALID_INPUT);
+}
+
+// Cell geometry from the bounding box.  The cell edge carries a margin so that
+// every pair within r_cut lies in adjacent cells despite float32 rounding of
+// the cell index: h >= r_cut * (1 + 2^-10) + extent * 2^-20.
+__device__ void compute_geometry(const Geo& in, float r_cut, float cell_scale, uint32_t cell_cap, Geo& out) {
+  double lo[3], hi[3];
+  const bool empty = in.n_sel == 0 || in.bbox_key[0] > in.bbox_key[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = empty ? 0.0 : (double)key2f(in.bbox_key[a]);
+    hi[a] = empty ? 0.0 : (double)key2f(in.bbox_key[3 + a]);
+  }
+  double ext = 0.0;
+  for (int a = 0; a < 3; ++a) ext = fmax(ext, hi[a] - lo[a]);
+  double h = (double)r_cut * (double)cell_scale * (1.0 + 1.0 / 1024.0) + ext * (1.0 / 1048576.0);
+  uint32_t dims[3] = {1, 1, 1};
+  for (int it = 0; it < 256; ++it) {
+    double tot = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      double d = floor((hi[a] - lo[a]) / h) + 1.0;
+      d = fmin(d, 2147483648.0);
+      dims[a] = (uint32_t)d;
+      tot *= d;
+    }
+    if (tot <= (double)cell_cap) break;
+    h *= 1.2599210498948732;  // 2^(1/3): halve the cell count
+  }
+  for (int a = 0; a < 3; ++a) {
+    out.origin[a] = (float)lo[a];
+    out.dims[a] = dims[a];
+  }
+  out.h = (float)h;
+  out.inv_h = (float)(1.0 / h);
+  out.n_cells = dims[0] * dims[1] * dims[2];
+}
+
+// Every block computes the same geometry; block 0 publishes it; all zero the counts.
+__global__ void __launch_bounds__(kThreads) k_geometry_zero(Geo* geo, float r_cut, float cell_scale, uint32_t cell_cap,
+                                                            uint32_t* __restrict__ count) {
+  Geo g = *geo;
+  compute_geometry(g, r_cut, cell_scale, cell_cap, g);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) geo->origin[a] = g.origin[a], geo->dims[a] = g.dims[a];
+    geo->h = g.h;
+    geo->inv_h = g.inv_h;
+    geo->n_cells = g.n_cells;
+  }
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += gridDim.x * blockDim.x) count[c] = 0;
+}
+
+// Cell index and rank (arrival order within the cell) of every selected ion.
+__global__ void __launch_bounds__(kThreads) k_count(const float* __restrict__ xyz, const uint32_t* __restrict__ sel,
+                                                    const Geo* __restrict__ geo, uint32_t* __restrict__ count,
+                                                    uint2* __restrict__ cr) {
+  const Geo g = *geo;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < g.n_sel; s += gridDim.x * blockDim.x) {
+    const uint32_t i = sel[s];
+    const uint32_t c = cell_of(g, xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2]);
+    cr[s] = make_uint2(c, atomicAdd(&count[c], 1u));
+  }
+}
+
+// Central ions: type in mask and d_srf >= dsrf_min, binned into the neighbour geometry.
+__global__ void __launch_bounds__(kThreads) k_central_select_count(const float* __restrict__ xyz,
+                                                                   const uint8_t* __restrict__ type,
+                                                                   const float* __restrict__ dsrf, int64_t n, Mask mask,
+                                                                   float dsrf_min, const Geo* __restrict__ ngeo,
+                                                                   Geo* cgeo, uint32_t* __restrict__ count,
+                                                                   uint32_t* __restrict__ sel, uint2* __restrict__ cr) {
+  const Geo g = *ngeo;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool s = false;
+    uint32_t c = 0;
+    if (i < n) {
+      s = in_mask(mask, type[i]) && (dsrf == nullptr || dsrf[i] >= dsrf_min);
+      if (s) {
+        const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        bad |= !finite3(x, y, z);
+        c = cell_of(g, x, y, z);
+      }
+    }
+    const uint32_t slot = warp_append(s, &cgeo->n_sel);
+    if (s) {
+      sel[slot] = (uint32_t)i;
+      cr[slot] = make_uint2(c, atomicAdd(&count[c], 1u));
+    }
+  }
+  if (bad) atomicCAS(&cgeo->status, 0, (int)PS_ERR_INVALID_INPUT);
+}
+
+__global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_t* __restrict__ count) {
+  const uint32_t nc = ngeo->n_cells;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *cgeo = *ngeo;
+    cgeo->n_sel = 0;
+    cgeo->status = 0;
+    cgeo->work_n = 0;
+    cgeo->work_next = 0;
+  }
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) count[c] = 0;
+}
+
+// ---- exclusive scan of the cell counts ------------------------------------
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t& total) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    if (lane < nw) s_warp[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t prefix = warp ? s_warp[warp - 1] : 0u;
+  total = s_warp[nw - 1];
+  __syncthreads();
+  return prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ count,
+                                                             const Geo* __restrict__ geo, uint32_t* __restrict__ part) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t nc = geo->n_cells;
+  const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
+  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint32_t c0 = t * kScanTile + threadIdx.x * kScanItems;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += (c0 + k < nc) ? count[c0 + k] : 0u;
+    uint32_t total;
+    block_exclusive_scan(sum, s_warp, total);
+    if (threadIdx.x == 0) part[t] = total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(uint32_t* __restrict__ part, const Geo* __restrict__ geo,
+                                                             uint32_t* __restrict__ start) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t nc = geo->n_cells;
+  const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
+  uint32_t carry = 0;
+  for (uint32_t b = 0; b < tiles; b += blockDim.x) {
+    const uint32_t t = b + threadIdx.x;
+    const uint32_t v = t < tiles ? part[t] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(v, s_warp, total);
+    if (t < tiles) part[t] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) start[nc] = carry;  // end sentinel: number of records
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ count,
+                                                             const uint32_t* __restrict__ part, Geo* geo,
+                                                             uint32_t* __restrict__ start, uint32_t* __restrict__ work) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t nc = geo->n_cells;
+  const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
+  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint32_t c0 = t * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = (c0 + k < nc) ? count[c0 + k] : 0u;
+      sum += v[k];
+    }
+    uint32_t total;
+    uint32_t run = part[t] + block_exclusive_scan(sum, s_warp, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (c0 + k < nc) start[c0 + k] = run;
+      run += v[k];
+      if (work != nullptr) {
+        const bool ne = (c0 + k < nc) && v[k] > 0;
+        const uint32_t slot = warp_append(ne, &geo->work_n);
+        if (ne) work[slot] = c0 + k;
+      }
+    }
+  }
+}
+
+// Scatter the selected ions to their sorted slot.
+__global__ void __launch_bounds__(kThreads) k_scatter(const float* __restrict__ xyz, const uint32_t* __restrict__ sel,
+                                                      const uint2* __restrict__ cr, const uint32_t* __restrict__ start,
+                                                      const Geo* __restrict__ cnt, float4* __restrict__ rec) {
+  const uint32_t ns = cnt->n_sel;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
+    const uint32_t i = sel[s];
+    const uint2 c = cr[s];
+    const int64_t b = 3 * (int64_t)i;
+    rec[start[c.x] + c.y] = make_float4(xyz[b], xyz[b + 1], xyz[b + 2], __uint_as_float(i));
+  }
+}
+
+static int grid_blocks(const ps_grid* g, int per_sm) { return g->num_sms * per_sm; }
+
+static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStream_t s) {
+  const int nb = grid_blocks(g, 1);
+  k_scan_tiles<<<nb, kScanThreads, 0, s>>>(L.count, geo, g->scan_part);
+  k_scan_parts<<<1, kScanThreads, 0, s>>>(g->scan_part, geo, L.start);
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(L.count, g->scan_part, geo, L.start, with_work ? L.work : nullptr);
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cudaStream_t s) {
+  Mask m;
+  for (int w = 0; w < 4; ++w) m.w[w] = nbr_mask[w];
+  Geo* geo = g->nbr.geo;
+  k_reset<<<1, 32, 0, s>>>(geo);
+  if (g->n > 0) k_select_bbox<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, g->n, m, g->sel, geo);
+  k_geometry_zero<<<grid_blocks(g, 4), kThreads, 0, s>>>(geo, r_cut, g->cell_scale, g->cell_cap, g->nbr.count);
+  k_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, geo, g->nbr.count, g->cr);
+  int rc = scan_cells(g, g->nbr, geo, false, s);
+  if (rc) return rc;
+  k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec);
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s) {
+  Mask m;
+  for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w];
+  k_central_reset<<<grid_blocks(g, 4), kThreads, 0, s>>>(g->nbr.geo, g->ctr.geo, g->ctr.count);
+  if (g->n > 0)
+    k_central_select_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, dsrf, g->n, m, dsrf_min,
+                                                                    g->nbr.geo, g->ctr.geo, g->ctr.count, g->sel, g->cr);
+  int rc = scan_cells(g, g->ctr, g->ctr.geo, true, s);
+  if (rc) return rc;
+  k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec);
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+}  // namespace ps
