@@ -1,0 +1,468 @@
+#!/usr/bin/env python
+"""Benchmark of the exact kNN + RDF spatial-statistics path on one GB300.
+
+Default workload: the ~8.07e6-ion needle (tip radius 20 nm, half-angle
+10 deg, height 100 nm, 30 ions/nm^3, Al3Sc precipitates), type combinations
+Sc-Sc and Si-Si, k in {1, 5, 10}, RDF on r = [0, 0.01, 2] nm, central ions
+with d_srf >= 2 nm.  One step = for each combination: build the neighbour
+cell grid (binner) and run the kNN + RDF query (central list + query
+kernel), i.e. every step of the exact path, with inputs resident in HBM.
+
+value   = ion queries (central ions evaluated, summed over the combinations
+          and over ranks) per second of device time.
+e2e     = the same metric through the public Python API with the inputs in
+          pinned host memory: H2D copy + both combinations + D2H of results.
+roofline: the dominant kernel family, timed with CUDA events on its stream
+          in the timed region, against the measured HBM copy bandwidth.
+cpu_baseline: the oracle (single-threaded C) on a bounded z-slab sample.
+
+--impl reference runs the oracle as the comparison arm on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+WORKLOADS = {
+    "needle8m": dict(
+        desc="needle 8.07e6 ions (r_tip 20 nm, 10 deg, h 100 nm, 30/nm^3, Al3Sc precipitates); Sc-Sc + Si-Si; "
+             "kNN k=1,5,10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
+        combos=[("Sc-Sc", [1], [1]), ("Si-Si", [2], [2])], ks=[1, 5, 10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
+    "cylinder200k": dict(
+        desc="Poisson cylinder 2e5 ions (R 10 nm, H 15.9 nm, 40/nm^3); all-all; kNN k=1 + RDF r=[0,0.01,2] nm; "
+             "d_srf>=1 nm",
+        combos=[("all-all", "all", "all")], ks=[1], spec=(0.0, 0.01, 2.0), dsrf_min=1.0),
+}
+
+
+def make_cloud(name: str, seed_offset: int = 0):
+    from paper_2004_05188_gb300 import specimen
+
+    if name == "needle8m":
+        return specimen.needle(specimen.needle_8m_params(seed=2 + seed_offset))
+    if name == "cylinder200k":
+        return specimen.cylinder_small(seed=1 + seed_offset)
+    raise ValueError(name)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax = float(parts[1])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle arm (cpu baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def slab_sample(xyz, t, d, frac: float, halo: float):
+    """A z-slab holding `frac` of the z-extent: its ions plus a halo of neighbours; halo ions are not central."""
+    z = xyz[:, 2]
+    zlo, zhi = float(z.min()), float(z.max())
+    z0 = zlo + 0.5 * (zhi - zlo) * (1.0 - frac)
+    z1 = z0 + frac * (zhi - zlo)
+    keep = (z >= z0 - halo) & (z < z1 + halo)
+    core = (z >= z0) & (z < z1)
+    ds = np.where(core[keep], d[keep], np.float32(-1e30)).astype(np.float32)
+    return xyz[keep], t[keep], ds
+
+
+def oracle_step(orc, cloud, wl):
+    xyz, t, d = cloud
+    r0, dr, nb = wl["bins"]
+    n = 0
+    for _, ctr, nbr in wl["combos"]:
+        r = orc.spatstat(xyz, t, d, ctr, nbr, wl["dsrf_min"], r0, dr, nb, wl["ks"])
+        n += r["n_central"]
+    return n
+
+
+def oracle_sample(wl_name, wl, cloud, target_s=1.0):
+    """Bounded sample of the workload for the oracle: a z-slab whose single-threaded run takes ~target_s."""
+    import oracle as orc
+
+    xyz, t, d = cloud
+    frac = 0.02
+    while True:
+        samp = slab_sample(xyz, t, d, frac, wl["bins"][1] * wl["bins"][2])
+        t0 = time.perf_counter()
+        nq = oracle_step(orc, samp, wl)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * target_s or frac >= 1.0:
+            break
+        frac = min(1.0, frac * max(2.0, 0.5 * target_s / max(dt, 1e-3)))
+    return orc, samp, frac, nq, dt
+
+
+def run_reference(args, wl_name, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cloud = make_cloud(wl_name)
+    orc, samp, frac, nq, _ = oracle_sample(wl_name, wl, cloud, target_s=1.0)
+    for _ in range(args.warmup):
+        oracle_step(orc, samp, wl)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        nq = oracle_step(orc, samp, wl)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    v = nq * args.steps / T
+    line = {
+        "impl": "reference", "metric": "ion-queries/s (exact kNN+RDF)", "value": v, "unit": "ion-queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": f"z-slab with {frac:.3f} of the height (+2 nm halo)"},
+        "cpu_baseline": {"value": v, "unit": "ion-queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"z-slab {frac:.3f} of the needle height, {nq} centrals per step"},
+        "e2e": {"value": v, "unit": "ion-queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(kid: str, st: dict) -> float:
+    """Bytes the kernel family must move per step (reads + writes of its role), summed over the combinations."""
+    N = st["n_ions"]
+    tot = 0.0
+    for c in st["combos"]:
+        nn, nc, cells, ntm = c["n_nbr"], c["n_central"], c["n_cells"], c["n_ctr_typed"]
+        if kid == "select":
+            tot += N * 1 + nn * 12 + nn * 4
+        elif kid == "central":
+            tot += cells * 4 + N * 1 + ntm * 4 + nc * 12 + nc * 12
+        elif kid == "count":
+            tot += nn * (4 + 12 + 8)
+        elif kid == "scatter":
+            tot += nn * (4 + 8 + 12 + 4 + 16) + nc * (4 + 8 + 12 + 4 + 16)
+        elif kid == "scan":
+            tot += 2 * cells * (4 + 4 + 4 + 4)
+        elif kid == "geometry":
+            tot += cells * 4
+        elif kid == "query":
+            tot += nn * 16 + nc * 16 + 2 * cells * 4
+    return tot
+
+
+def run_gpu(args, wl_name, wl):
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    cloud = make_cloud(wl_name, seed_offset=1000 * rank)
+    xyz, t, d = cloud
+    N = xyz.shape[0]
+    X = torch.from_numpy(xyz).to(dev)
+    T = torch.from_numpy(t).to(dev)
+    D = torch.from_numpy(d).to(dev)
+    bins = wl["bins"]
+    r_cut = float(np.float32(bins[0] + bins[1] * bins[2]))
+    grids = [ps.Grid(N, args.cell_scale, args.dense_min) for _ in wl["combos"]]
+    nk = len(wl["ks"])
+    outs = []
+    for _ in wl["combos"]:
+        outs.append(dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
+                         knn=torch.empty((nk, bins[2]), dtype=torch.int64, device=dev),
+                         meta=torch.empty(ps.META_HEAD + 2 * nk, dtype=torch.int64, device=dev)))
+    stream = torch.cuda.current_stream()
+
+    def step(Xs=X, Ts=T, Ds=D):
+        for (name, ctr, nbr), g, o in zip(wl["combos"], grids, outs):
+            g.build(Xs, Ts, nbr, r_cut)
+            ps.spatstat(g, Ds, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # correctness of the configuration before timing: device status words
+    step()
+    torch.cuda.synchronize()
+    st = {"n_ions": N, "combos": []}
+    n_queries = 0
+    n_pairs = 0
+    for (name, ctr, nbr), g, o in zip(wl["combos"], grids, outs):
+        meta = o["meta"].cpu().numpy()
+        if meta[3] != 0:
+            raise RuntimeError(f"device status {meta[3]} for {name}")
+        info = g.info()
+        ctr_set = range(256) if ctr == "all" else ctr
+        ntm = int(np.isin(t, list(ctr_set)).sum())
+        st["combos"].append(dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
+                                 n_ctr_typed=ntm, n_pairs=int(meta[1])))
+        n_queries += int(meta[0])
+        n_pairs += int(meta[1])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # dominant kernel family and its per-launch time: an eager pass with CUDA
+    # events around every launch of the library (not the graph-timed region)
+    fams = ["reset", "select", "geometry", "count", "scan", "scatter", "central", "query", "epilogue"]
+    ps.prof_enable(fams)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = {f: ps.prof_read(f) for f in fams}
+    ps.prof_enable([])
+    shares = {f: v[1] for f, v in prof.items()}
+    dom = max(shares, key=shares.get)
+    dom_n, dom_ms = prof[dom]
+    eager_ms = None
+
+    # the timed step: the whole pass captured once in a CUDA graph, replayed per step
+    graph = None
+    kernels_per_step = None
+    if not args.no_graph:
+        lc = ps.launch_count()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        kernels_per_step = ps.launch_count() - lc
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+
+    def timed_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                           int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    sampler.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    lc0 = ps.launch_count()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (not timed)
+        ev0[k].record(stream)
+        timed_step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = ps.launch_count() - lc0 if graph is None else kernels_per_step * args.steps
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    T_ms = float(sum(step_ms))
+    if dist is not None:
+        tt = torch.tensor([T_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        T_ms = float(tt.item())
+        qq = torch.tensor([n_queries, n_pairs], dtype=torch.float64, device=dev)
+        dist.all_reduce(qq)
+        tot_q, tot_p = float(qq[0].item()), float(qq[1].item())
+    else:
+        tot_q, tot_p = float(n_queries), float(n_pairs)
+    value = tot_q * args.steps / (T_ms * 1e-3)
+
+    # ---- e2e through the public API, inputs in pinned host memory ----
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(xyz).pin_memory()
+        Th = torch.from_numpy(t).pin_memory()
+        Dh = torch.from_numpy(d).pin_memory()
+        res_h = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in outs]
+        Xd, Td, Dd = (X, T, D) if graph is not None else (torch.empty_like(X), torch.empty_like(T), torch.empty_like(D))
+
+        def e2e_step():
+            Xd.copy_(Xh, non_blocking=True)
+            Td.copy_(Th, non_blocking=True)
+            Dd.copy_(Dh, non_blocking=True)
+            if graph is not None:
+                graph.replay()  # the captured pass reads X, T, D
+            else:
+                step(Xd, Td, Dd)
+            for o, h in zip(outs, res_h):
+                for k in o:
+                    h[k].copy_(o[k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            e0[k].record(stream)
+            e2e_step()
+            e1[k].record(stream)
+        torch.cuda.synchronize()
+        E_ms = float(sum(a.elapsed_time(b) for a, b in zip(e0, e1)))
+        if dist is not None:
+            tt = torch.tensor([E_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            E_ms = float(tt.item())
+        h2d = xyz.nbytes + t.nbytes + d.nbytes
+        d2h = sum(v.numel() * v.element_size() for o in outs for v in o.values())
+        e2e = {"value": tot_q * args.steps / (E_ms * 1e-3), "unit": "ion-queries/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": E_ms / args.steps}
+
+    # ---- roofline of the dominant kernel family ----
+    peak, peak_kind = load_peaks()
+    alg = algorithmic_bytes(dom, st)
+    launches_per_step = max(1, dom_n // max(1, args.steps))
+    per_launch_bytes = alg / launches_per_step
+    avg_ms = dom_ms / max(1, dom_n)
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "avg_launch_us": avg_ms * 1e3, "launches": dom_n, "timing": "CUDA events around each launch, eager pass",
+                "time_share": shares[dom] / max(1e-12, sum(shares.values())),
+                "shares": {k: round(v / max(1e-12, sum(shares.values())), 4) for k, v in shares.items()}}
+
+    # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        orc, samp, frac, nq, _ = oracle_sample(wl_name, wl, cloud, target_s=2.0)
+        reps = 0
+        t0 = time.perf_counter()
+        while reps < 3 or time.perf_counter() - t0 < 10.0:
+            oracle_step(orc, samp, wl)
+            reps += 1
+            if time.perf_counter() - t0 > 30.0:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": nq * reps / dt, "unit": "ion-queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"z-slab with {frac:.3f} of the height (+2 nm halo), {nq} centrals, {reps} runs"}
+
+    if rank == 0:
+        line = {
+            "metric": "ion-queries/s (exact kNN+RDF)", "value": value, "unit": "ion-queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n_ions": N, "centrals_per_step": n_queries,
+                       "cell_scale": args.cell_scale, "dense_min": args.dense_min,
+                       "neighbour_pairs_per_step": n_pairs, "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{world} (independent specimens, no collective)"},
+            "neighbour_pairs_per_s": tot_p * args.steps / (T_ms * 1e-3),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps, "clocks": clocks, "wall_s_timed_loop": wall,
+            "cuda_graph": graph is not None,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    for g in grids:
+        g.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="needle8m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
+    ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    wl = dict(WORKLOADS[args.workload])
+    r0, dr, stop = wl["spec"]
+    wl["bins"] = (r0, dr, int(round((stop - r0) / dr)))
+    if args.impl == "reference":
+        return run_reference(args, args.workload, wl)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return run_gpu(args, args.workload, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

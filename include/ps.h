@@ -95,9 +95,11 @@ typedef struct {
 /* Options for a cell grid.  struct_size = sizeof(ps_grid_opts). */
 typedef struct {
   uint32_t struct_size;
-  float cell_scale; /* cell edge = r_cut * cell_scale; 0 = default (1.0); must be >= 1 */
-  uint32_t block;   /* query threads per block; 0 = default */
-  uint32_t reserved;
+  float cell_scale;   /* cell edge = r_cut * cell_scale; 0 = default (1.0).  >= 1: the 27 cells
+                         around a cell are searched; in [0.5, 1): the 125 cells within two cells */
+  uint32_t block;     /* reserved (0) */
+  uint32_t dense_min; /* cells with at least this many centrals use the CTA kernel that stages the
+                         neighbour cells in shared memory with bulk copies; 0 = never */
 } ps_grid_opts;
 
 typedef struct ps_grid ps_grid; /* opaque; owns its device scratch */
@@ -176,6 +178,36 @@ PS_API int ps_knn_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
 /* RDF histogram: ps_spatstat with n_k = 0.  d_meta is uint64 [PS_META_LEN(0)]. */
 PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
                 uint64_t* d_hist, uint64_t* d_meta, void* stream);
+
+/*
+ * Launch accounting and per-kernel timing (no counterpart in the paper; the
+ * paper reports wall-clock per task).
+ *   ps_launch_count   kernels this library has launched in this process.
+ *   ps_prof_enable    record a CUDA event pair on the launching stream around
+ *                     every launch of the kernel families in `kid_mask`
+ *                     (bit 1 << PS_KID_*); 0 disables.  Resets the tallies.
+ *                     Synchronises the device.
+ *   ps_prof_read      launches and summed event time (ms) of one family since
+ *                     ps_prof_enable; waits for the recorded events.
+ */
+typedef enum {
+  PS_KID_RESET = 1,      /* grid reset */
+  PS_KID_SELECT = 2,     /* neighbour-set selection + bounding box */
+  PS_KID_GEOMETRY = 3,   /* cell geometry + zeroing of the counts */
+  PS_KID_COUNT = 4,      /* cell index + rank of the neighbours */
+  PS_KID_SCAN = 5,       /* exclusive scan of cell counts (3 launches) */
+  PS_KID_SCATTER = 6,    /* counting-sort scatter */
+  PS_KID_CENTRAL = 7,    /* central reset + selection + cell rank */
+  PS_KID_QUERY = 8,      /* exact kNN + RDF query */
+  PS_KID_EPILOGUE = 9,   /* meta epilogue */
+  PS_KID_SOFT_FWD = 10,  /* smoothed RDF forward */
+  PS_KID_SOFT_BWD = 11,  /* smoothed RDF adjoint */
+  PS_KID_BATCH = 12,     /* batched sweep kernels */
+  PS_KID_COUNT_ = 13
+} ps_kernel_id;
+PS_API uint64_t ps_launch_count(void);
+PS_API int ps_prof_enable(uint32_t kid_mask);
+PS_API int ps_prof_read(uint32_t kid, uint64_t* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

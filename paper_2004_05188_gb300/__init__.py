@@ -67,7 +67,7 @@ class Bins(ctypes.Structure):
 
 class GridOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("cell_scale", ctypes.c_float), ("block", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("dense_min", ctypes.c_uint32)]
 
 
 class GridInfo(ctypes.Structure):
@@ -106,10 +106,9 @@ def lib():
     L.ps_spatstat.argtypes = [P, P, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_knn_hist.argtypes = [P, P, P, f32, u32, Bins, P, P, P, P]
     L.ps_rdf_hist.argtypes = [P, P, P, f32, Bins, P, P, P]
-    for name in header_functions():
-        fn = getattr(L, name)
-        if fn.restype is ctypes.c_int and name != "ps_last_error":
-            fn.restype = i32
+    L.ps_launch_count.restype = ctypes.c_uint64
+    L.ps_prof_enable.argtypes = [u32]
+    L.ps_prof_read.argtypes = [u32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
     _lib = L
     return L
 
@@ -117,6 +116,31 @@ def lib():
 def _check(rc: int):
     if rc != PS_OK:
         raise PSError(rc, lib().ps_last_error().decode(errors="replace"))
+
+
+KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
+           soft_bwd=11, batch=12)
+
+
+def launch_count() -> int:
+    """Kernels launched by libps in this process."""
+    return int(lib().ps_launch_count())
+
+
+def prof_enable(kernels=()) -> None:
+    """Time every launch of the named kernel families with CUDA events (resets the tallies)."""
+    mask = 0
+    for k in kernels:
+        mask |= 1 << KID[k]
+    _check(lib().ps_prof_enable(mask))
+
+
+def prof_read(kernel: str):
+    """(launches, total ms) of one kernel family since prof_enable."""
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(lib().ps_prof_read(KID[kernel], ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 def edges(r0: float, dr: float, n_bins: int) -> np.ndarray:
@@ -161,8 +185,10 @@ def _check_cloud(xyz, type_, dsrf=None):
 class Grid:
     """A cell grid over the neighbour set of one cloud (ps_grid_create / ps_grid_build)."""
 
-    def __init__(self, n_max: int, cell_scale: float = 1.0):
-        opts = GridOpts(ctypes.sizeof(GridOpts), float(cell_scale), 0, 0)
+    def __init__(self, n_max: int, cell_scale: float = 1.0, dense_min: int = 0):
+        """cell_scale: cell edge / r_cut (>= 1: 27-cell search; [0.5, 1): 125-cell search).
+        dense_min: cells with at least this many centrals use the shared-memory staged kernel (0: never)."""
+        opts = GridOpts(ctypes.sizeof(GridOpts), float(cell_scale), 0, int(dense_min))
         h = ctypes.c_void_p()
         _check(lib().ps_grid_create(int(n_max), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h

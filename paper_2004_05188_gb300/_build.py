@@ -18,6 +18,12 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 
+# Translation units whose float32 arithmetic must not be contracted into FMA:
+# the exact path compares squared distances bit for bit, and ptxas fuses packed
+# (f32x2) multiplies and adds even when they carry an explicit rounding modifier.
+NO_FMA = {"ps_query.cu", "ps_grid.cu", "ps_batch.cu"}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -34,15 +40,31 @@ def _stale(out: str) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every csrc/*.cu in parallel, then link libps.so.  Returns its path."""
+    """Compile every csrc/*.cu in parallel, then link libps.so.  Returns its path.
+
+    Concurrent callers (one per rank) serialise on a lock file."""
+    import fcntl
+
     if not force and not _stale(LIB):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            if force or _stale(LIB):
+                _build_locked(verbose, extra_flags)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+    return LIB
+
+
+def _build_locked(verbose, extra_flags):
     srcs = _sources()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [NVCC, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+        fmad = ["-fmad=false", "-Xptxas", "--fmad=false"] if os.path.basename(src) in NO_FMA else []
+        cmd = [NVCC, *ARCH, *FLAGS, *fmad, *extra_flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,4 +82,3 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
-    return LIB

@@ -71,13 +71,17 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
     if (opts->cell_scale != 0.0f) cell_scale = opts->cell_scale;
     if (opts->struct_size >= offsetof(ps_grid_opts, block) + sizeof(uint32_t)) block = opts->block;
   }
-  if (!(cell_scale >= 1.0f) || !std::isfinite(cell_scale)) return fail(PS_ERR_INVALID_ARG, "cell_scale must be >= 1");
+  if (!(cell_scale >= 0.5f) || !std::isfinite(cell_scale))
+    return fail(PS_ERR_INVALID_ARG, "cell_scale must be >= 0.5");
   ps_grid* g = new (std::nothrow) ps_grid();
   if (!g) return fail(PS_ERR_OOM, "host allocation failed");
   g->n_max = n_max > 0 ? n_max : 1;
   g->cell_scale = cell_scale;
+  g->stencil = cell_scale >= 1.0f ? 1 : 2;
   g->block = block;
-  const int64_t cap = g->n_max / 2 > 65536 ? g->n_max / 2 : 65536;
+  if (opts && opts->struct_size >= sizeof(ps_grid_opts)) g->dense_min = opts->dense_min ? opts->dense_min : 0xFFFFFFFFu;
+  const int64_t cap0 = g->stencil == 2 ? g->n_max * 2 : g->n_max / 2;
+  const int64_t cap = cap0 > 65536 ? cap0 : 65536;
   g->cell_cap = (uint32_t)(cap < (int64_t)1 << 31 ? cap : (int64_t)1 << 31);
   g->scan_tiles_cap = (g->cell_cap + 4095) / 4096;
   cudaError_t e = cudaGetDevice(&g->device);
@@ -96,6 +100,8 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   const size_t o_sel = take(nm * 4), o_cr = take(nm * 8);
   const size_t o_ncount = take(cc * 4), o_nstart = take((cc + 1) * 4), o_nrec = take(nm * 16);
   const size_t o_ccount = take(cc * 4), o_cstart = take((cc + 1) * 4), o_crec = take(nm * 16), o_cwork = take(cc * 4);
+  g->item_cap = (uint32_t)(cc + nm / 32 + 2);
+  const size_t o_witem = take((size_t)g->item_cap * 8);
   const size_t o_part = take((size_t)g->scan_tiles_cap * 4), o_ngeo = take(sizeof(Geo)), o_cgeo = take(sizeof(Geo));
   void* base = nullptr;
   e = cudaMalloc(&base, off);
@@ -115,6 +121,7 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   g->ctr.start = reinterpret_cast<uint32_t*>(b + o_cstart);
   g->ctr.rec = reinterpret_cast<float4*>(b + o_crec);
   g->ctr.work = reinterpret_cast<uint32_t*>(b + o_cwork);
+  g->ctr.witem = reinterpret_cast<uint2*>(b + o_witem);
   g->ctr.geo = reinterpret_cast<Geo*>(b + o_cgeo);
   g->scan_part = reinterpret_cast<uint32_t*>(b + o_part);
   e = cudaMemset(g->nbr.geo, 0, sizeof(Geo));

@@ -11,6 +11,7 @@
 // Pipeline (all on the device, no host synchronisation):
 //   reset -> select + bounding box -> geometry + zero counts -> count ranks
 //   -> exclusive scan (tiles, tile prefixes, apply) -> scatter
+// The selection kernels read 16 type labels per thread (one 16-byte load).
 #include <cstring>
 
 #include "ps_internal.cuh"
@@ -21,6 +22,7 @@ constexpr int kThreads = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr uint32_t kScanTile = kScanThreads * kScanItems;
+constexpr int kGroup = 16;  // ions per thread in the selection kernels
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
@@ -35,6 +37,38 @@ __device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t* counter) {
   return base + __popc(bal & ((1u << lane_id()) - 1u));
 }
 
+// warp-aggregated append of `cnt` items per lane (full warp): returns this lane's first slot
+__device__ __forceinline__ uint32_t warp_append_n(uint32_t cnt, uint32_t* counter) {
+  uint32_t x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane_id() >= (uint32_t)o) x += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+  uint32_t base = 0;
+  if (lane_id() == 31 && total) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + x - cnt;
+}
+
+// the 16 type labels of group g (ions 16g .. 16g+15); `valid` masks the labels past n
+__device__ __forceinline__ void load_types16(const uint8_t* __restrict__ type, int64_t n, int64_t g, bool vec,
+                                             uint8_t (&t)[kGroup], uint32_t& valid) {
+  const int64_t i0 = g * kGroup;
+  const int64_t left = n - i0;
+  valid = left >= kGroup ? 0xFFFFu : ((1u << (uint32_t)left) - 1u);
+  if (vec && left >= kGroup) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(type + i0));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < kGroup; ++k) t[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+  } else {
+#pragma unroll
+    for (int k = 0; k < kGroup; ++k) t[k] = (k < left) ? type[i0 + k] : 0;
+  }
+}
+
 __global__ void k_reset(Geo* geo) {
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
@@ -43,35 +77,66 @@ __global__ void k_reset(Geo* geo) {
     }
     geo->n_sel = 0;
     geo->status = 0;
-    geo->work_n = 0;
-    geo->work_next = 0;
+    geo->work_n = geo->work_n2 = 0;
+    geo->work_next = geo->work_next2 = 0;
+  }
+}
+
+__device__ __forceinline__ void box_add(float (&lo)[3], float (&hi)[3], bool& bad, float x, float y, float z) {
+  if (finite3(x, y, z)) {
+    lo[0] = fminf(lo[0], x), hi[0] = fmaxf(hi[0], x);
+    lo[1] = fminf(lo[1], y), hi[1] = fmaxf(hi[1], y);
+    lo[2] = fminf(lo[2], z), hi[2] = fmaxf(hi[2], z);
+  } else {
+    bad = true;
   }
 }
 
 // Select the ions of the neighbour set, append their indices, reduce the bounding box.
 __global__ void __launch_bounds__(kThreads) k_select_bbox(const float* __restrict__ xyz, const uint8_t* __restrict__ type,
-                                                          int64_t n, Mask mask, uint32_t* __restrict__ sel, Geo* geo) {
+                                                          int64_t n, Mask mask, bool vec, uint32_t* __restrict__ sel,
+                                                          Geo* geo) {
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
+  const int64_t groups = (n + kGroup - 1) / kGroup;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    bool s = false;
-    if (i < n) {
-      s = in_mask(mask, type[i]);
-      if (s) {
-        const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        if (finite3(x, y, z)) {
-          lo[0] = fminf(lo[0], x), hi[0] = fmaxf(hi[0], x);
-          lo[1] = fminf(lo[1], y), hi[1] = fmaxf(hi[1], y);
-          lo[2] = fminf(lo[2], z), hi[2] = fmaxf(hi[2], z);
-        } else {
-          bad = true;
-        }
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < groups; base += stride) {
+    const int64_t g = base + threadIdx.x;
+    uint32_t m = 0;
+    if (g < groups) {
+      uint8_t t[kGroup];
+      uint32_t valid;
+      load_types16(type, n, g, vec, t, valid);
+#pragma unroll
+      for (int k = 0; k < kGroup; ++k) m |= (in_mask(mask, t[k]) ? 1u : 0u) << k;
+      m &= valid;
+    }
+    const uint32_t cnt = __popc(m);
+    uint32_t slot = warp_append_n(cnt, &geo->n_sel);
+    const int64_t i0 = g * kGroup;
+    if (cnt >= 4 && vec && m == 0xFFFFu) {
+      // a full group: read its 192 bytes of coordinates as 12 float4
+      const float4* p = reinterpret_cast<const float4*>(xyz + 3 * i0);
+      float c[3 * kGroup];
+#pragma unroll
+      for (int q = 0; q < 3 * kGroup / 4; ++q) {
+        const float4 v = __ldg(p + q);
+        c[4 * q] = v.x, c[4 * q + 1] = v.y, c[4 * q + 2] = v.z, c[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int k = 0; k < kGroup; ++k) {
+        box_add(lo, hi, bad, c[3 * k], c[3 * k + 1], c[3 * k + 2]);
+        sel[slot + k] = (uint32_t)(i0 + k);
+      }
+    } else {
+      while (m) {
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        const int64_t i = i0 + k;
+        box_add(lo, hi, bad, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+        sel[slot++] = (uint32_t)i;
       }
     }
-    const uint32_t slot = warp_append(s, &geo->n_sel);
-    if (s) sel[slot] = (uint32_t)i;
   }
   // block reduction of the box
   __shared__ float s_lo[3][kThreads / 32], s_hi[3][kThreads / 32];
@@ -102,8 +167,9 @@ __global__ void __launch_bounds__(kThreads) k_select_bbox(const float* __restric
 }
 
 // Cell geometry from the bounding box.  The cell edge carries a margin so that
-// every pair within r_cut lies in adjacent cells despite float32 rounding of
-// the cell index: h >= r_cut * (1 + 2^-10) + extent * 2^-20.
+// every pair within r_cut lies within `stencil` cells of each other despite
+// float32 rounding of the cell index: stencil * h >= r_cut * (1 + 2^-10) +
+// extent * 2^-20 (cell_scale >= 1/stencil).
 __device__ void compute_geometry(const Geo& in, float r_cut, float cell_scale, uint32_t cell_cap, Geo& out) {
   double lo[3], hi[3];
   const bool empty = in.n_sel == 0 || in.bbox_key[0] > in.bbox_key[3];
@@ -135,18 +201,24 @@ __device__ void compute_geometry(const Geo& in, float r_cut, float cell_scale, u
   out.n_cells = dims[0] * dims[1] * dims[2];
 }
 
-// Every block computes the same geometry; block 0 publishes it; all zero the counts.
+// One thread per block computes the geometry; block 0 publishes it; all zero the counts.
 __global__ void __launch_bounds__(kThreads) k_geometry_zero(Geo* geo, float r_cut, float cell_scale, uint32_t cell_cap,
                                                             uint32_t* __restrict__ count) {
-  Geo g = *geo;
-  compute_geometry(g, r_cut, cell_scale, cell_cap, g);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int a = 0; a < 3; ++a) geo->origin[a] = g.origin[a], geo->dims[a] = g.dims[a];
-    geo->h = g.h;
-    geo->inv_h = g.inv_h;
-    geo->n_cells = g.n_cells;
+  __shared__ uint32_t s_nc;
+  if (threadIdx.x == 0) {
+    Geo g = *geo;
+    compute_geometry(g, r_cut, cell_scale, cell_cap, g);
+    s_nc = g.n_cells;
+    if (blockIdx.x == 0) {
+      for (int a = 0; a < 3; ++a) geo->origin[a] = g.origin[a], geo->dims[a] = g.dims[a];
+      geo->h = g.h;
+      geo->inv_h = g.inv_h;
+      geo->n_cells = g.n_cells;
+    }
   }
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += gridDim.x * blockDim.x) count[c] = 0;
+  __syncthreads();
+  const uint32_t nc = s_nc;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) count[c] = 0;
 }
 
 // Cell index and rank (arrival order within the cell) of every selected ion.
@@ -165,28 +237,58 @@ __global__ void __launch_bounds__(kThreads) k_count(const float* __restrict__ xy
 __global__ void __launch_bounds__(kThreads) k_central_select_count(const float* __restrict__ xyz,
                                                                    const uint8_t* __restrict__ type,
                                                                    const float* __restrict__ dsrf, int64_t n, Mask mask,
-                                                                   float dsrf_min, const Geo* __restrict__ ngeo,
+                                                                   float dsrf_min, bool vec, const Geo* __restrict__ ngeo,
                                                                    Geo* cgeo, uint32_t* __restrict__ count,
                                                                    uint32_t* __restrict__ sel, uint2* __restrict__ cr) {
   const Geo g = *ngeo;
   bool bad = false;
+  const int64_t groups = (n + kGroup - 1) / kGroup;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    bool s = false;
-    uint32_t c = 0;
-    if (i < n) {
-      s = in_mask(mask, type[i]) && (dsrf == nullptr || dsrf[i] >= dsrf_min);
-      if (s) {
-        const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        bad |= !finite3(x, y, z);
-        c = cell_of(g, x, y, z);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < groups; base += stride) {
+    const int64_t gi = base + threadIdx.x;
+    uint32_t m = 0;
+    const int64_t i0 = gi * kGroup;
+    if (gi < groups) {
+      uint8_t t[kGroup];
+      uint32_t valid;
+      load_types16(type, n, gi, vec, t, valid);
+#pragma unroll
+      for (int k = 0; k < kGroup; ++k) m |= (in_mask(mask, t[k]) ? 1u : 0u) << k;
+      m &= valid;
+      if (dsrf != nullptr && m) {
+        uint32_t keep = 0;
+        if (m == 0xFFFFu && vec) {
+          const float4* p = reinterpret_cast<const float4*>(dsrf + i0);
+#pragma unroll
+          for (int q = 0; q < kGroup / 4; ++q) {
+            const float4 v = __ldg(p + q);
+            keep |= ((v.x >= dsrf_min) ? 1u : 0u) << (4 * q);
+            keep |= ((v.y >= dsrf_min) ? 1u : 0u) << (4 * q + 1);
+            keep |= ((v.z >= dsrf_min) ? 1u : 0u) << (4 * q + 2);
+            keep |= ((v.w >= dsrf_min) ? 1u : 0u) << (4 * q + 3);
+          }
+        } else {
+          uint32_t mm = m;
+          while (mm) {
+            const int k = __ffs(mm) - 1;
+            mm &= mm - 1;
+            keep |= ((dsrf[i0 + k] >= dsrf_min) ? 1u : 0u) << k;
+          }
+        }
+        m &= keep;
       }
     }
-    const uint32_t slot = warp_append(s, &cgeo->n_sel);
-    if (s) {
+    uint32_t slot = warp_append_n(__popc(m), &cgeo->n_sel);
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t i = i0 + k;
+      const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+      bad |= !finite3(x, y, z);
+      const uint32_t c = cell_of(g, x, y, z);
       sel[slot] = (uint32_t)i;
       cr[slot] = make_uint2(c, atomicAdd(&count[c], 1u));
+      ++slot;
     }
   }
   if (bad) atomicCAS(&cgeo->status, 0, (int)PS_ERR_INVALID_INPUT);
@@ -198,8 +300,8 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     *cgeo = *ngeo;
     cgeo->n_sel = 0;
     cgeo->status = 0;
-    cgeo->work_n = 0;
-    cgeo->work_next = 0;
+    cgeo->work_n = cgeo->work_n2 = 0;
+    cgeo->work_next = cgeo->work_next2 = 0;
   }
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) count[c] = 0;
 }
@@ -265,9 +367,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_parts(uint32_t* __restric
   if (threadIdx.x == 0) start[nc] = carry;  // end sentinel: number of records
 }
 
+// Warp items of a cell with n centrals: n <= 3 gives one item (the lanes of
+// the warp split the candidates of each central); otherwise ceil(n/32)
+// balanced batches of at most 32 centrals (one lane per central).
+__device__ __forceinline__ uint32_t items_of(uint32_t n) { return n == 0 ? 0u : (n <= 3 ? 1u : (n + 31u) / 32u); }
+
+// Writes start[] and, for the central list, the work lists: cells with at
+// least dense_min centrals go to `work` (CTA kernel), the others are split
+// into warp items (cell, first << 6 | count) in `witem`.
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ count,
                                                              const uint32_t* __restrict__ part, Geo* geo,
-                                                             uint32_t* __restrict__ start, uint32_t* __restrict__ work) {
+                                                             uint32_t* __restrict__ start, uint32_t* __restrict__ work,
+                                                             uint2* __restrict__ witem, uint32_t dense_min) {
   __shared__ uint32_t s_warp[32];
   const uint32_t nc = geo->n_cells;
   const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
@@ -285,10 +396,29 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
     for (int k = 0; k < kScanItems; ++k) {
       if (c0 + k < nc) start[c0 + k] = run;
       run += v[k];
-      if (work != nullptr) {
-        const bool ne = (c0 + k < nc) && v[k] > 0;
-        const uint32_t slot = warp_append(ne, &geo->work_n);
-        if (ne) work[slot] = c0 + k;
+    }
+    if (work != nullptr) {
+      uint32_t n_items = 0;
+#pragma unroll
+      for (int k = 0; k < kScanItems; ++k) {
+        const bool dense = (c0 + k < nc) && v[k] >= dense_min;
+        const uint32_t s1 = warp_append(dense, &geo->work_n);
+        if (dense) work[s1] = c0 + k;
+        if (!dense) n_items += items_of(v[k]);
+      }
+      uint32_t slot = warp_append_n(n_items, &geo->work_n2);
+#pragma unroll
+      for (int k = 0; k < kScanItems; ++k) {
+        if (v[k] >= dense_min) continue;
+        const uint32_t m = items_of(v[k]);
+        if (m == 0) continue;
+        const uint32_t base = v[k] / m, rem = v[k] % m;
+        uint32_t first = 0;
+        for (uint32_t q = 0; q < m; ++q) {
+          const uint32_t cnt = base + (q < rem ? 1u : 0u);
+          witem[slot++] = make_uint2(c0 + k, (first << 6) | cnt);
+          first += cnt;
+        }
       }
     }
   }
@@ -309,11 +439,15 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const float* __restrict__ 
 
 static int grid_blocks(const ps_grid* g, int per_sm) { return g->num_sms * per_sm; }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStream_t s) {
   const int nb = grid_blocks(g, 1);
-  k_scan_tiles<<<nb, kScanThreads, 0, s>>>(L.count, geo, g->scan_part);
-  k_scan_parts<<<1, kScanThreads, 0, s>>>(g->scan_part, geo, L.start);
-  k_scan_apply<<<nb, kScanThreads, 0, s>>>(L.count, g->scan_part, geo, L.start, with_work ? L.work : nullptr);
+  PS_LAUNCH(PS_KID_SCAN, s, k_scan_tiles<<<nb, kScanThreads, 0, s>>>(L.count, geo, g->scan_part));
+  PS_LAUNCH(PS_KID_SCAN, s, k_scan_parts<<<1, kScanThreads, 0, s>>>(g->scan_part, geo, L.start));
+  PS_LAUNCH(PS_KID_SCAN, s,
+            k_scan_apply<<<nb, kScanThreads, 0, s>>>(L.count, g->scan_part, geo, L.start,
+                                                     with_work ? L.work : nullptr, L.witem, g->dense_min));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -322,13 +456,18 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
   Mask m;
   for (int w = 0; w < 4; ++w) m.w[w] = nbr_mask[w];
   Geo* geo = g->nbr.geo;
-  k_reset<<<1, 32, 0, s>>>(geo);
-  if (g->n > 0) k_select_bbox<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, g->n, m, g->sel, geo);
-  k_geometry_zero<<<grid_blocks(g, 4), kThreads, 0, s>>>(geo, r_cut, g->cell_scale, g->cell_cap, g->nbr.count);
-  k_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, geo, g->nbr.count, g->cr);
+  const bool vec = aligned16(g->type) && aligned16(g->xyz);
+  PS_LAUNCH(PS_KID_RESET, s, k_reset<<<1, 32, 0, s>>>(geo));
+  if (g->n > 0)
+    PS_LAUNCH(PS_KID_SELECT, s,
+              k_select_bbox<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, g->n, m, vec, g->sel, geo));
+  PS_LAUNCH(PS_KID_GEOMETRY, s,
+            k_geometry_zero<<<grid_blocks(g, 4), kThreads, 0, s>>>(geo, r_cut, g->cell_scale, g->cell_cap, g->nbr.count));
+  PS_LAUNCH(PS_KID_COUNT, s, k_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, geo, g->nbr.count, g->cr));
   int rc = scan_cells(g, g->nbr, geo, false, s);
   if (rc) return rc;
-  k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec);
+  PS_LAUNCH(PS_KID_SCATTER, s,
+            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -336,13 +475,18 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s) {
   Mask m;
   for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w];
-  k_central_reset<<<grid_blocks(g, 4), kThreads, 0, s>>>(g->nbr.geo, g->ctr.geo, g->ctr.count);
+  const bool vec = aligned16(g->type) && aligned16(g->xyz) && (dsrf == nullptr || aligned16(dsrf));
+  PS_LAUNCH(PS_KID_CENTRAL, s,
+            k_central_reset<<<grid_blocks(g, 4), kThreads, 0, s>>>(g->nbr.geo, g->ctr.geo, g->ctr.count));
   if (g->n > 0)
-    k_central_select_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, dsrf, g->n, m, dsrf_min,
-                                                                    g->nbr.geo, g->ctr.geo, g->ctr.count, g->sel, g->cr);
+    PS_LAUNCH(PS_KID_CENTRAL, s,
+              k_central_select_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, dsrf, g->n, m, dsrf_min,
+                                                                              vec, g->nbr.geo, g->ctr.geo, g->ctr.count,
+                                                                              g->sel, g->cr));
   int rc = scan_cells(g, g->ctr, g->ctr.geo, true, s);
   if (rc) return rc;
-  k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec);
+  PS_LAUNCH(PS_KID_SCATTER, s,
+            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

@@ -17,6 +17,16 @@ void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+void prof_begin(uint32_t kid, cudaStream_t s);
+void prof_end(uint32_t kid, cudaStream_t s);
+// every kernel launch of the library goes through this (launch count + optional event timing)
+#define PS_LAUNCH(kid, s, ...)  \
+  do {                          \
+    ps::prof_begin((kid), (s)); \
+    __VA_ARGS__;                \
+    ps::prof_end((kid), (s));   \
+  } while (0)
+
 #define PS_CUDA(call)                                   \
   do {                                                  \
     cudaError_t e_ = (call);                            \
@@ -35,9 +45,10 @@ struct Geo {
   uint32_t n_sel;   // ions in the set
   int32_t bbox_key[6];  // order-preserving int keys of min xyz, max xyz
   int32_t status;   // device-side ps_status
-  uint32_t work_n;  // non-empty cells in the work list
-  uint32_t work_next;  // persistent-kernel work counter
-  uint32_t pad[2];
+  uint32_t work_n;     // dense cells in work[] (CTA-staged kernel)
+  uint32_t work_n2;    // warp items in witem[] (warp kernel)
+  uint32_t work_next;  // persistent-kernel work counters
+  uint32_t work_next2;
 };
 
 // A sorted cell list: count / start per cell and the sorted records.
@@ -45,7 +56,8 @@ struct CellList {
   uint32_t* count = nullptr;   // [cell_cap]
   uint32_t* start = nullptr;   // [cell_cap + 1]
   float4* rec = nullptr;       // [n_max]: x, y, z, original index bits
-  uint32_t* work = nullptr;    // [cell_cap]: non-empty cells
+  uint32_t* work = nullptr;    // [cell_cap]: dense cells
+  uint2* witem = nullptr;      // [item_cap]: (cell, first central << 6 | count) warp items
   Geo* geo = nullptr;          // device
 };
 
@@ -65,6 +77,9 @@ struct ps_grid {
   float r_cut = 0.0f;
   bool built = false;
   // scratch shared by both builds
+  uint32_t dense_min = 0xFFFFFFFFu;  // cells with at least this many centrals go to the CTA-staged kernel
+  uint32_t item_cap = 0;       // capacity of the warp item list
+  int stencil = 1;             // neighbour cells searched on each side (1: cell >= r_cut, 2: cell >= r_cut/2)
   uint32_t* sel = nullptr;     // [n_max] selected ion indices
   uint2* cr = nullptr;         // [n_max] (cell, rank) of selected ions
   uint32_t* scan_part = nullptr;  // [scan tiles]
@@ -132,6 +147,45 @@ __device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, f
   const float dy = __fsub_rn(by, ay);
   const float dz = __fsub_rn(bz, az);
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// packed pairs of float32 (two IEEE round-to-nearest results per instruction)
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// two squared distances at once, same operation order and rounding as dist2():
+// packed differences and squares, then scalar round-to-nearest additions (a packed
+// add after a packed multiply can be fused into an FMA by the assembler)
+__device__ __forceinline__ void dist2_x2(unsigned long long px, unsigned long long py, unsigned long long pz,
+                                         unsigned long long qx, unsigned long long qy, unsigned long long qz,
+                                         float& d2a, float& d2b) {
+  const unsigned long long dx = f2_sub(qx, px), dy = f2_sub(qy, py), dz = f2_sub(qz, pz);
+  float xa, xb, ya, yb, za, zb;
+  f2_unpack(f2_mul(dx, dx), xa, xb);
+  f2_unpack(f2_mul(dy, dy), ya, yb);
+  f2_unpack(f2_mul(dz, dz), za, zb);
+  d2a = __fadd_rn(__fadd_rn(xa, ya), za);
+  d2b = __fadd_rn(__fadd_rn(xb, yb), zb);
 }
 
 // ---------------------------------------------------------------------------

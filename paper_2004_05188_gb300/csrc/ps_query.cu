@@ -3,25 +3,34 @@
 // The paper evaluates one spherical ROI per central ion and machines the ROIs
 // off with a dynamic schedule, each thread keeping its own result buffers that
 // are merged afterwards (Suppl. "Customized user defined batch processing
-// queues").  Here a persistent CTA takes one non-empty central cell at a time
-// from a device work counter (the dynamic schedule), stages the 27 neighbour
-// cells of that cell into shared memory with bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier), and evaluates every central of
-// the cell against the staged records.  Results go to per-CTA shared-memory
-// histograms (the per-thread buffers) that are added to the uint64 global
-// histograms once per CTA.
+// queues").  Here the ROIs of one cell of the grid share their candidates: the
+// cells within `stencil` cells of it (27 cells for cells of edge >= r_cut, 125
+// for cells of edge >= r_cut/2), read as x-contiguous runs of sorted records.
+// Two persistent kernels take work from device counters (the dynamic
+// schedule):
 //
-// Two mappings of centrals to threads, chosen per cell:
-//   A (dense cells):  one thread per central, the whole block walks the
-//                     staged candidates in lock step (shared-memory broadcast);
-//   B (sparse cells): one warp per central, lanes stride over the candidates,
-//                     per-lane top-k lists merged by warp shuffles.
-// Both keep the k smallest squared distances in registers (sorted insertion).
+//   warp kernel  one warp per item = (cell, batch of <= 32 centrals).  The
+//                candidates are read 32 at a time with one coalesced load into
+//                a per-warp shared buffer (the next batch is prefetched into
+//                registers meanwhile); each lane holds one central and walks
+//                the buffer (shared-memory broadcast).  Items with <= 3
+//                centrals let the lanes split the candidates of each central
+//                and merge their top-k lists by shuffles.
+//   CTA kernel   for cells with >= dense_min centrals (an option): one CTA per
+//                cell; the runs are staged into shared memory with bulk
+//                asynchronous copies (cp.async.bulk, completion on an mbarrier)
+//                and one thread per central walks them.
+//
+// Each thread keeps the k smallest squared distances in registers (sorted
+// insertion).  Counts go to per-CTA shared-memory histograms (the per-thread
+// buffers) added to the uint64 global histograms when the CTA finishes.
 #include <cstring>
 
 #include "ps_internal.cuh"
 
 namespace ps {
+
+constexpr int kMaxRuns = 25;  // (2 * stencil + 1)^2 for stencil <= 2
 
 struct QueryArgs {
   const float4* nrec;
@@ -30,12 +39,14 @@ struct QueryArgs {
   const float4* crec;
   const uint32_t* cstart;
   const uint32_t* cwork;
+  const uint2* witem;
   Geo* cgeo;
+  int stencil;
   double r0, dr;
   uint32_t n_bins;
   uint32_t n_k;
-  uint32_t k_need;  // max requested k
-  uint32_t stage_cap;  // float4 records per staging chunk
+  uint32_t k_need;     // max requested k
+  uint32_t stage_cap;  // float4 records per staging chunk (CTA kernel)
   uint32_t ks[PS_MAX_KLIST];
   uint64_t* rdf;
   uint64_t* knn;
@@ -44,8 +55,6 @@ struct QueryArgs {
   uint32_t* nwithin;
   int64_t n;  // ions in the cloud (stride of kth)
 };
-
-constexpr uint32_t kModeAMin = 64;  // cells with at least this many centrals use mapping A
 
 template <int K>
 __device__ __forceinline__ void topk_insert(float (&top)[K], float x) {
@@ -65,13 +74,17 @@ __device__ __forceinline__ float topk_get(const float (&top)[K], uint32_t idx) {
   return v;
 }
 
-// bin b in [0, nb) with sE[b] <= d2 < sE[b+1]; caller guarantees sE[0] <= d2 < sE[nb]
+// bin b in [0, nb) with sE[b] <= d2 < sE[b+1]; caller guarantees sE[0] <= d2 < sE[nb].
+// The guess from an approximate square root is checked against the exact edge
+// table; the (rare) wrong guess is walked to the right bin.
 __device__ __forceinline__ uint32_t bin_index(float d2, const float* sE, uint32_t nb, float r0f, float inv_dr) {
-  const float g = (__fsqrt_rn(d2) - r0f) * inv_dr;
-  int b = (int)g;
+  const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+  int b = (int)((d - r0f) * inv_dr);
   b = b < 0 ? 0 : (b >= (int)nb ? (int)nb - 1 : b);
-  while (b > 0 && d2 < sE[b]) --b;
-  while (b + 1 < (int)nb && d2 >= sE[b + 1]) ++b;
+  if (d2 < sE[b] || d2 >= sE[b + 1]) {
+    while (b > 0 && d2 < sE[b]) --b;
+    while (b + 1 < (int)nb && d2 >= sE[b + 1]) ++b;
+  }
   return (uint32_t)b;
 }
 
@@ -97,59 +110,322 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k,
   return L;
 }
 
+// Per-CTA result buffers in shared memory.
+template <bool RDF>
+struct Hist {
+  float* sE;
+  uint32_t* s_rdf;
+  uint32_t* s_knn;
+  uint32_t* s_kmeta;
+  float Emax, E0, r0f, inv_dr;
+  uint32_t nb;
+
+  __device__ void init(const QueryArgs& a, unsigned char* smem, uint32_t stage_cap) {
+    const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap);
+    sE = reinterpret_cast<float*>(smem + L.off_E);
+    s_rdf = reinterpret_cast<uint32_t*>(smem + L.off_rdf);
+    s_knn = reinterpret_cast<uint32_t*>(smem + L.off_knn);
+    s_kmeta = reinterpret_cast<uint32_t*>(smem + L.off_kmeta);
+    nb = a.n_bins;
+    // edge table: the same double formula as the host, E[b] = (float)((r0 + b*dr)^2)
+    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
+      const double e = __dadd_rn(a.r0, __dmul_rn((double)b, a.dr));
+      sE[b] = __double2float_rn(__dmul_rn(e, e));
+    }
+    if (RDF)
+      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_rdf[b] = 0;
+    for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x) s_knn[b] = 0;
+    for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x) s_kmeta[b] = 0;
+    __syncthreads();
+    Emax = sE[nb];
+    E0 = sE[0];
+    r0f = (float)a.r0;
+    inv_dr = (float)(1.0 / a.dr);
+  }
+
+  // one in-range pair (d2 < Emax): RDF bin (shared, or global when `glob`)
+  __device__ __forceinline__ void pair(const QueryArgs& a, float d2, bool glob, uint64_t& binned, uint64_t& below) {
+    if (!RDF) return;
+    if (d2 >= E0) {
+      const uint32_t b = bin_index(d2, sE, nb, r0f, inv_dr);
+      if (glob)
+        atomicAdd((unsigned long long*)&a.rdf[b], 1ull);
+      else
+        atomicAdd(&s_rdf[b], 1u);
+      ++binned;
+    } else {
+      ++below;
+    }
+  }
+
+  // the k-th distance D of one central for the q-th requested k
+  __device__ __forceinline__ void kth(const QueryArgs& a, uint32_t q, float D, uint32_t idx, bool glob) {
+    if (a.kth) a.kth[(int64_t)q * a.n + idx] = D;
+    uint32_t* sp;
+    unsigned long long* gp;
+    if (!(D < Emax)) {
+      sp = &s_kmeta[2 * q];
+      gp = (unsigned long long*)&a.meta[PS_META_HEAD + 2 * q];
+    } else if (D < E0) {
+      sp = &s_kmeta[2 * q + 1];
+      gp = (unsigned long long*)&a.meta[PS_META_HEAD + 2 * q + 1];
+    } else {
+      const uint32_t b = bin_index(D, sE, nb, r0f, inv_dr);
+      sp = &s_knn[q * nb + b];
+      gp = (unsigned long long*)&a.knn[q * nb + b];
+    }
+    if (glob)
+      atomicAdd(gp, 1ull);
+    else
+      atomicAdd(sp, 1u);
+  }
+
+  // add the shared counters to the global histograms and clear them (whole CTA)
+  __device__ void flush(const QueryArgs& a) {
+    __syncthreads();
+    if (RDF)
+      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+        if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], (unsigned long long)s_rdf[b]), s_rdf[b] = 0;
+    for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x)
+      if (s_knn[b]) atomicAdd((unsigned long long*)&a.knn[b], (unsigned long long)s_knn[b]), s_knn[b] = 0;
+    for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x)
+      if (s_kmeta[b])
+        atomicAdd((unsigned long long*)&a.meta[PS_META_HEAD + b], (unsigned long long)s_kmeta[b]), s_kmeta[b] = 0;
+    __syncthreads();
+  }
+};
+
+__device__ __forceinline__ void add_pair_counters(const QueryArgs& a, uint64_t binned, uint64_t below) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    binned += __shfl_xor_sync(0xffffffffu, binned, o);
+    below += __shfl_xor_sync(0xffffffffu, below, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (binned) atomicAdd((unsigned long long*)&a.meta[PS_META_N_PAIRS], (unsigned long long)binned);
+    if (below) atomicAdd((unsigned long long*)&a.meta[PS_META_N_BELOW], (unsigned long long)below);
+  }
+}
+
+// cell c -> run r of its stencil: the x-contiguous records of cells (cx-s .. cx+s, cy+dy, cz+dz)
+__device__ __forceinline__ void cell_run(const QueryArgs& a, const Geo& ng, uint32_t c, uint32_t r, uint32_t& src,
+                                         uint32_t& len) {
+  const int s = a.stencil, w = 2 * s + 1;
+  const uint32_t cx = c % ng.dims[0], cy = (c / ng.dims[0]) % ng.dims[1], cz = c / (ng.dims[0] * ng.dims[1]);
+  const int y = (int)cy + (int)(r % w) - s, z = (int)cz + (int)(r / w) - s;
+  src = 0;
+  len = 0;
+  if ((int)r < w * w && y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2]) {
+    const uint32_t xlo = cx >= (uint32_t)s ? cx - s : 0;
+    const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
+    const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+    src = a.nstart[row + xlo];
+    len = a.nstart[row + xhi + 1] - src;
+  }
+}
+
+__device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(~0u)); }
+
+// ---------------------------------------------------------------------------
+// warp kernel: one warp per (cell, <= 32 centrals) item
+// ---------------------------------------------------------------------------
 template <int KMAX, bool RDF>
-__global__ void __launch_bounds__(256) k_query(const QueryArgs a) {
+__global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_bound;
+  __shared__ float4 s_buf[8][32];
+  __shared__ float s_hits[8][32 * 32];  // per warp: the in-range hits of one batch
+  __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
+  constexpr int KK = KMAX > 0 ? KMAX : 1;
+  Hist<RDF> H;
+  if (threadIdx.x == 0) s_bound = 0;
+  H.init(a, smem, 0);
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const Geo ng = *a.ngeo;
+  const uint32_t n_items = a.cgeo->work_n2;
+  const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
+  uint64_t my_binned = 0, my_below = 0;
+  float4* buf = s_buf[w];
+  float* wlist = s_hits[w];
+  uint32_t* rsrc = s_rsrc[w];
+  uint32_t* rpre = s_rpre[w];
+
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(&a.cgeo->work_next2, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const uint2 it = a.witem[item];
+    const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
+    const uint32_t c0 = a.cstart[c] + first;
+    // run table: sources and prefix counts of the candidate runs
+    uint32_t src = 0, len = 0;
+    cell_run(a, ng, c, lane, src, len);
+    uint32_t pre = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= (uint32_t)o) pre += y;
+    }
+    const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
+    __syncwarp();
+    if (lane < (uint32_t)n_runs) {
+      rsrc[lane] = src;
+      rpre[lane + 1] = pre;
+    }
+    if (lane == 0) rpre[0] = 0;
+    __syncwarp();
+    // shared counters take at most 2^31 increments in total; beyond that this warp writes to global
+    unsigned long long old = 0;
+    const unsigned long long inc = (unsigned long long)cnt * ((unsigned long long)n_cand + 1);
+    if (lane == 0) old = atomicAdd(&s_bound, inc);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    const bool glob = old + inc >= (1ull << 31);
+
+    // record at virtual candidate position pos (runs concatenated); rr is a run hint, nondecreasing in pos
+    auto fetch = [&](uint32_t pos, int& rr) -> float4 {
+      if (pos >= n_cand) return far_record();
+      while (pos >= rpre[rr + 1]) ++rr;
+      return __ldg(a.nrec + rsrc[rr] + (pos - rpre[rr]));
+    };
+
+    if (cnt > 3) {
+      // One lane per central.  32 candidates per coalesced load, staged in the warp's
+      // buffer as 16 interleaved pairs (xa xb ya yb za zb wa wb) and tested two at a time
+      // with packed float32 math.  kNN: each lane updates its own top-k inline (the
+      // threshold test rarely passes once the list is full).  RDF: in-range hits are
+      // appended to a warp-wide list (ballot + popc give each hit its slot) and binned
+      // after the batch by all 32 lanes together.
+      const bool valid = lane < cnt;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) p = a.crec[c0 + lane];
+      const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
+      const float emax = valid ? H.Emax : -INFINITY;  // lanes without a central never hit
+      const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
+      const uint32_t lt = (1u << lane) - 1u;
+      float top[KK];
+#pragma unroll
+      for (int t = 0; t < KK; ++t) top[t] = INFINITY;
+      uint32_t within = 0;
+      int rr = 0;
+      float4 nxt = fetch(lane, rr);
+      float* bf = reinterpret_cast<float*>(buf);
+      for (uint32_t b = 0; b < n_cand; b += 32) {
+        __syncwarp();
+        {
+          float* d = bf + (lane >> 1) * 8 + (lane & 1);
+          d[0] = nxt.x, d[2] = nxt.y, d[4] = nxt.z, d[6] = nxt.w;
+        }
+        __syncwarp();
+        nxt = fetch(b + 32 + lane, rr);
+        uint32_t nh = 0;  // hits in the warp list (uniform)
+#pragma unroll 4
+        for (int t = 0; t < 16; ++t) {
+          const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
+          const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
+          float d2a, d2b;
+          dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
+          float wa, wb;
+          f2_unpack(zw.y, wa, wb);
+          const bool ha = d2a < emax && __float_as_uint(wa) != pidx;
+          const bool hb = d2b < emax && __float_as_uint(wb) != pidx;
+          within += (uint32_t)ha + (uint32_t)hb;
+          if (KMAX > 0) {
+            if (ha && d2a < top[KK - 1]) topk_insert(top, d2a);
+            if (hb && d2b < top[KK - 1]) topk_insert(top, d2b);
+          }
+          if (RDF) {
+            const uint32_t ba = __ballot_sync(0xffffffffu, ha);
+            if (ha) wlist[nh + __popc(ba & lt)] = d2a;
+            nh += __popc(ba);
+            const uint32_t bb = __ballot_sync(0xffffffffu, hb);
+            if (hb) wlist[nh + __popc(bb & lt)] = d2b;
+            nh += __popc(bb);
+          }
+        }
+        if (RDF) {
+          __syncwarp();
+          for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], glob, my_binned, my_below);
+        }
+      }
+      if (valid) {
+        if (a.nwithin) a.nwithin[pidx] = within;
+        if (KMAX > 0)
+          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx, glob);
+      }
+    } else {
+      // few centrals: the lanes split the candidates of each central
+      for (uint32_t ci = 0; ci < cnt; ++ci) {
+        const float4 p = a.crec[c0 + ci];
+        const uint32_t pidx = __float_as_uint(p.w);
+        float top[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) top[t] = INFINITY;
+        uint32_t within = 0;
+        int rr = 0;
+        for (uint32_t b = 0; b < n_cand; b += 32) {
+          const float4 q = fetch(b + lane, rr);
+          const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+          if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
+            ++within;
+            H.pair(a, d2, glob, my_binned, my_below);
+            if (KMAX > 0) topk_insert(top, d2);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) within += __shfl_xor_sync(0xffffffffu, within, o);
+        if (lane == 0 && a.nwithin) a.nwithin[pidx] = within;
+        if (KMAX > 0) {
+          // merge the 32 sorted lane lists: pop the warp minimum k_need times
+          for (uint32_t rank = 0; rank < a.k_need; ++rank) {
+            float m = top[0];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const uint32_t bal = __ballot_sync(0xffffffffu, top[0] == m);
+            if (lane == (uint32_t)(__ffs(bal) - 1)) {
+#pragma unroll
+              for (int t = 0; t < KK - 1; ++t) top[t] = top[t + 1];
+              top[KK - 1] = INFINITY;
+            }
+            if (lane == 0)
+              for (uint32_t q = 0; q < a.n_k; ++q)
+                if (a.ks[q] == rank + 1) H.kth(a, q, m, pidx, glob);
+          }
+        }
+      }
+    }
+  }
+  H.flush(a);
+  add_pair_counters(a, my_binned, my_below);
+}
+
+// ---------------------------------------------------------------------------
+// CTA kernel: one CTA per dense cell, runs staged in shared memory by bulk copies
+// ---------------------------------------------------------------------------
+template <int KMAX, bool RDF>
+__global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t s_item;
-  __shared__ uint32_t s_run_src[9], s_run_len[9];
+  __shared__ uint32_t s_run_src[kMaxRuns], s_run_len[kMaxRuns];
   __shared__ int s_timeout;
+  constexpr int KK = KMAX > 0 ? KMAX : 1;
 
-  const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, a.stage_cap);
-  float* sE = reinterpret_cast<float*>(smem + L.off_E);
-  uint32_t* s_rdf = reinterpret_cast<uint32_t*>(smem + L.off_rdf);
-  uint32_t* s_knn = reinterpret_cast<uint32_t*>(smem + L.off_knn);
-  uint32_t* s_kmeta = reinterpret_cast<uint32_t*>(smem + L.off_kmeta);
-  float4* s_cand = reinterpret_cast<float4*>(smem + L.off_stage);
-
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const uint32_t nb = a.n_bins;
-  // edge table: the same double formula as the host, E[b] = (float)((r0 + b*dr)^2)
-  for (uint32_t b = tid; b <= nb; b += blockDim.x) {
-    const double e = __dadd_rn(a.r0, __dmul_rn((double)b, a.dr));
-    sE[b] = __double2float_rn(__dmul_rn(e, e));
-  }
-  if (RDF)
-    for (uint32_t b = tid; b < nb; b += blockDim.x) s_rdf[b] = 0;
-  for (uint32_t b = tid; b < a.n_k * nb; b += blockDim.x) s_knn[b] = 0;
-  for (uint32_t b = tid; b < 2 * a.n_k; b += blockDim.x) s_kmeta[b] = 0;
-  if (tid == 0) {
+  Hist<RDF> H;
+  if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
     s_timeout = 0;
   }
-  __syncthreads();
-
-  const float Emax = sE[nb], E0 = sE[0];
-  const float r0f = (float)a.r0, inv_dr = (float)(1.0 / a.dr);
+  H.init(a, smem, a.stage_cap);
+  float4* s_cand = reinterpret_cast<float4*>(smem + smem_layout(a.n_bins, a.n_k, RDF, a.stage_cap).off_stage);
+  const uint32_t tid = threadIdx.x;
   const Geo ng = *a.ngeo;
   const uint32_t work_n = a.cgeo->work_n;
+  const uint32_t n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   uint32_t phase = 0;
   uint64_t my_binned = 0, my_below = 0;
   uint64_t bound = 0;  // upper bound of any shared counter since the last flush (uniform)
-
-  auto flush = [&]() {
-    __syncthreads();
-    if (RDF)
-      for (uint32_t b = tid; b < nb; b += blockDim.x)
-        if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], (unsigned long long)s_rdf[b]), s_rdf[b] = 0;
-    for (uint32_t b = tid; b < a.n_k * nb; b += blockDim.x)
-      if (s_knn[b]) atomicAdd((unsigned long long*)&a.knn[b], (unsigned long long)s_knn[b]), s_knn[b] = 0;
-    for (uint32_t b = tid; b < 2 * a.n_k; b += blockDim.x)
-      if (s_kmeta[b])
-        atomicAdd((unsigned long long*)&a.meta[PS_META_HEAD + b], (unsigned long long)s_kmeta[b]), s_kmeta[b] = 0;
-    __syncthreads();
-  };
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(&a.cgeo->work_next, 1u);
@@ -157,53 +433,37 @@ __global__ void __launch_bounds__(256) k_query(const QueryArgs a) {
     const uint32_t item = s_item;
     if (item >= work_n || s_timeout) break;
     const uint32_t c = a.cwork[item];
-    const uint32_t cx = c % ng.dims[0], cy = (c / ng.dims[0]) % ng.dims[1], cz = c / (ng.dims[0] * ng.dims[1]);
     const uint32_t c0 = a.cstart[c], n_c = a.cstart[c + 1] - c0;
-    if (tid < 9) {
-      const int y = (int)cy + (int)(tid % 3) - 1, z = (int)cz + (int)(tid / 3) - 1;
-      uint32_t src = 0, len = 0;
-      if (y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2]) {
-        const uint32_t xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < ng.dims[0] ? cx + 1 : ng.dims[0] - 1;
-        const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
-        src = a.nstart[row + xlo];
-        len = a.nstart[row + xhi + 1] - src;
-      }
-      s_run_src[tid] = src;
-      s_run_len[tid] = len;
-    }
+    if (tid < n_runs) cell_run(a, ng, c, tid, s_run_src[tid], s_run_len[tid]);
     __syncthreads();
     uint32_t n_cand = 0;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) n_cand += s_run_len[r];
+    for (uint32_t r = 0; r < n_runs; ++r) n_cand += s_run_len[r];
 
     // bound the shared 32-bit counters: flush before they could overflow
     const uint64_t inc = (uint64_t)n_c * ((uint64_t)n_cand + 1);
     if (bound + inc >= (1ull << 31)) {
-      flush();
+      H.flush(a);
       bound = 0;
     }
     bound += inc;
 
-    const bool modeA = n_c >= kModeAMin;
-    const uint32_t batch = modeA ? blockDim.x : nwarps;
-    for (uint32_t cb = 0; cb < n_c; cb += batch) {
-      const uint32_t ci = cb + (modeA ? tid : warp);
+    for (uint32_t cb = 0; cb < n_c; cb += blockDim.x) {
+      const uint32_t ci = cb + tid;
       const bool valid = ci < n_c;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) p = a.crec[c0 + ci];
       const uint32_t pidx = __float_as_uint(p.w);
-      float top[KMAX > 0 ? KMAX : 1];
+      float top[KK];
 #pragma unroll
-      for (int t = 0; t < (KMAX > 0 ? KMAX : 1); ++t) top[t] = INFINITY;
+      for (int t = 0; t < KK; ++t) top[t] = INFINITY;
       uint32_t within = 0;
 
-      // walk the 9 runs in chunks of at most stage_cap records
+      // walk the runs in chunks of at most stage_cap records (padded to a multiple of 8 with far records)
       uint32_t r = 0, ro = 0;
-      while (r < 9) {
-        // assemble the next chunk (every thread computes the same pieces)
+      while (r < n_runs) {
         uint32_t chunk = 0;
         uint32_t rr = r, rro = ro;
-        while (rr < 9 && chunk < a.stage_cap) {
+        while (rr < n_runs && chunk < a.stage_cap) {
           const uint32_t len = s_run_len[rr];
           const uint32_t take = min(len - rro, a.stage_cap - chunk);
           chunk += take;
@@ -211,10 +471,12 @@ __global__ void __launch_bounds__(256) k_query(const QueryArgs a) {
           if (rro >= len) ++rr, rro = 0;
         }
         if (chunk == 0) break;
+        const uint32_t padded = (chunk + 7u) & ~7u;
         if (tid == 0) {
+          for (uint32_t t = chunk; t < padded; ++t) s_cand[t] = far_record();
           mbar_arrive_expect_tx(&bar, chunk * 16u);
           uint32_t dst = 0, q = r, qo = ro;
-          while (q < 9 && dst < chunk) {
+          while (q < n_runs && dst < chunk) {
             const uint32_t len = s_run_len[q];
             const uint32_t take = min(len - qo, chunk - dst);
             if (take) bulk_g2s(s_cand + dst, a.nrec + s_run_src[q] + qo, take * 16u, &bar);
@@ -229,37 +491,14 @@ __global__ void __launch_bounds__(256) k_query(const QueryArgs a) {
         phase ^= 1u;
 
         if (valid) {
-          if (modeA) {
-            for (uint32_t t = 0; t < chunk; ++t) {
-              const float4 q = s_cand[t];
+          for (uint32_t t0 = 0; t0 < padded; t0 += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float4 q = s_cand[t0 + u];
               const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-              if (d2 < Emax && __float_as_uint(q.w) != pidx) {
+              if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
                 ++within;
-                if (RDF) {
-                  if (d2 >= E0) {
-                    atomicAdd(&s_rdf[bin_index(d2, sE, nb, r0f, inv_dr)], 1u);
-                    ++my_binned;
-                  } else {
-                    ++my_below;
-                  }
-                }
-                if (KMAX > 0) topk_insert(top, d2);
-              }
-            }
-          } else {
-            for (uint32_t t = lane; t < chunk; t += 32) {
-              const float4 q = s_cand[t];
-              const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-              if (d2 < Emax && __float_as_uint(q.w) != pidx) {
-                ++within;
-                if (RDF) {
-                  if (d2 >= E0) {
-                    atomicAdd(&s_rdf[bin_index(d2, sE, nb, r0f, inv_dr)], 1u);
-                    ++my_binned;
-                  } else {
-                    ++my_below;
-                  }
-                }
+                H.pair(a, d2, false, my_binned, my_below);
                 if (KMAX > 0) topk_insert(top, d2);
               }
             }
@@ -267,71 +506,16 @@ __global__ void __launch_bounds__(256) k_query(const QueryArgs a) {
         }
         __syncthreads();  // the chunk buffer is reused next
       }
-
-      // finalize the batch's centrals
-      if (modeA) {
-        if (valid) {
-          if (a.nwithin) a.nwithin[pidx] = within;
-          if (KMAX > 0)
-            for (uint32_t q = 0; q < a.n_k; ++q) {
-              const float D = topk_get(top, a.ks[q] - 1);
-              if (a.kth) a.kth[(int64_t)q * a.n + pidx] = D;
-              if (!(D < Emax))
-                atomicAdd(&s_kmeta[2 * q], 1u);
-              else if (D < E0)
-                atomicAdd(&s_kmeta[2 * q + 1], 1u);
-              else
-                atomicAdd(&s_knn[q * nb + bin_index(D, sE, nb, r0f, inv_dr)], 1u);
-            }
-        }
-      } else {
-        // warp-level: total count and merge of the per-lane sorted lists
-        uint32_t w = within;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if (valid && lane == 0 && a.nwithin) a.nwithin[pidx] = w;
-        if (KMAX > 0) {
-          float Dk[PS_MAX_KLIST > 0 ? 1 : 1];
-          (void)Dk;
-          for (uint32_t rank = 0; rank < a.k_need; ++rank) {
-            float m = top[0];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            const uint32_t bal = __ballot_sync(0xffffffffu, top[0] == m);
-            if (lane == (uint32_t)(__ffs(bal) - 1)) {
-#pragma unroll
-              for (int t = 0; t < (KMAX > 0 ? KMAX : 1) - 1; ++t) top[t] = top[t + 1];
-              top[(KMAX > 0 ? KMAX : 1) - 1] = INFINITY;
-            }
-            if (valid && lane == 0)
-              for (uint32_t q = 0; q < a.n_k; ++q) {
-                if (a.ks[q] != rank + 1) continue;
-                if (a.kth) a.kth[(int64_t)q * a.n + pidx] = m;
-                if (!(m < Emax))
-                  atomicAdd(&s_kmeta[2 * q], 1u);
-                else if (m < E0)
-                  atomicAdd(&s_kmeta[2 * q + 1], 1u);
-                else
-                  atomicAdd(&s_knn[q * nb + bin_index(m, sE, nb, r0f, inv_dr)], 1u);
-              }
-          }
-        }
+      if (valid) {
+        if (a.nwithin) a.nwithin[pidx] = within;
+        if (KMAX > 0)
+          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx, false);
       }
     }
     __syncthreads();  // s_item and the run table are rewritten next
   }
-
-  flush();
-  // pair counters
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    my_binned += __shfl_xor_sync(0xffffffffu, my_binned, o);
-    my_below += __shfl_xor_sync(0xffffffffu, my_below, o);
-  }
-  if (lane == 0) {
-    if (my_binned) atomicAdd((unsigned long long*)&a.meta[PS_META_N_PAIRS], (unsigned long long)my_binned);
-    if (my_below) atomicAdd((unsigned long long*)&a.meta[PS_META_N_BELOW], (unsigned long long)my_below);
-  }
+  H.flush(a);
+  add_pair_counters(a, my_binned, my_below);
   if (tid == 0 && s_timeout) atomicCAS((int*)&a.cgeo->status, 0, (int)PS_ERR_TIMEOUT);
 }
 
@@ -346,27 +530,35 @@ __global__ void k_query_epilogue(const Geo* __restrict__ ngeo, const Geo* __rest
 }
 
 template <int KMAX, bool RDF>
-static int launch_query(const ps_grid* g, const QueryArgs& qa, uint32_t smem, cudaStream_t s) {
-  auto kern = k_query<KMAX, RDF>;
-  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
-  if (per_sm < 1) return fail(PS_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
-  kern<<<g->num_sms * per_sm, 256, smem, s>>>(qa);
+static int launch_query(const ps_grid* g, const QueryArgs& qa, uint32_t smem_cta, uint32_t smem_warp, cudaStream_t s) {
+  auto kw = k_query_warp<KMAX, RDF>;
+  PS_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp));
+  int per_sm_w = 0;
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, kw, 256, smem_warp));
+  if (per_sm_w < 1) return fail(PS_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
+  if (g->dense_min != 0xFFFFFFFFu) {
+    auto kc = k_query_cta<KMAX, RDF>;
+    PS_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta));
+    int per_sm_c = 0;
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kc, 256, smem_cta));
+    if (per_sm_c < 1) return fail(PS_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
+    PS_LAUNCH(PS_KID_QUERY, s, kc<<<g->num_sms * per_sm_c, 256, smem_cta, s>>>(qa));
+  }
+  PS_LAUNCH(PS_KID_QUERY, s, kw<<<g->num_sms * per_sm_w, 256, smem_warp, s>>>(qa));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
 template <bool RDF>
-static int dispatch_k(const ps_grid* g, const QueryArgs& qa, uint32_t smem, cudaStream_t s) {
+static int dispatch_k(const ps_grid* g, const QueryArgs& qa, uint32_t sc, uint32_t sw, cudaStream_t s) {
   const uint32_t k = qa.k_need;
-  if (k == 0) return RDF ? launch_query<0, RDF>(g, qa, smem, s) : PS_OK;
-  if (k <= 1) return launch_query<1, RDF>(g, qa, smem, s);
-  if (k <= 2) return launch_query<2, RDF>(g, qa, smem, s);
-  if (k <= 4) return launch_query<4, RDF>(g, qa, smem, s);
-  if (k <= 8) return launch_query<8, RDF>(g, qa, smem, s);
-  if (k <= 16) return launch_query<16, RDF>(g, qa, smem, s);
-  return launch_query<32, RDF>(g, qa, smem, s);
+  if (k == 0) return RDF ? launch_query<0, RDF>(g, qa, sc, sw, s) : PS_OK;
+  if (k <= 1) return launch_query<1, RDF>(g, qa, sc, sw, s);
+  if (k <= 2) return launch_query<2, RDF>(g, qa, sc, sw, s);
+  if (k <= 4) return launch_query<4, RDF>(g, qa, sc, sw, s);
+  if (k <= 8) return launch_query<8, RDF>(g, qa, sc, sw, s);
+  if (k <= 16) return launch_query<16, RDF>(g, qa, sc, sw, s);
+  return launch_query<32, RDF>(g, qa, sc, sw, s);
 }
 
 int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
@@ -380,7 +572,9 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.crec = g->ctr.rec;
   qa.cstart = g->ctr.start;
   qa.cwork = g->ctr.work;
+  qa.witem = g->ctr.witem;
   qa.cgeo = g->ctr.geo;
+  qa.stencil = g->stencil;
   qa.r0 = bins.r0;
   qa.dr = bins.dr;
   qa.n_bins = bins.n_bins;
@@ -405,7 +599,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s);
   if (rc) return rc;
 
-  // staging budget: two CTAs per SM
+  // staging budget of the CTA kernel: two CTAs per SM
   int dev_smem = 0;
   PS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
   const SmemLayout base = smem_layout(bins.n_bins, n_k, rdf, 0);
@@ -413,13 +607,14 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   if (base.total + 16 * 1024 > (uint32_t)dev_smem - 1024)
     return fail(PS_ERR_UNSUPPORTED, "too many bins x k values for shared memory");
   uint32_t stage_bytes = budget > base.total + 16 * 1024 ? budget - base.total : 16 * 1024;
-  qa.stage_cap = stage_bytes / 16;
-  const uint32_t smem = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap).total;
+  qa.stage_cap = (stage_bytes / 16) & ~7u;
+  const uint32_t smem_cta = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap).total;
+  const uint32_t smem_warp = base.total;
   if (n_k > 0 || rdf) {
-    rc = rdf ? dispatch_k<true>(g, qa, smem, s) : dispatch_k<false>(g, qa, smem, s);
+    rc = rdf ? dispatch_k<true>(g, qa, smem_cta, smem_warp, s) : dispatch_k<false>(g, qa, smem_cta, smem_warp, s);
     if (rc) return rc;
   }
-  k_query_epilogue<<<1, 32, 0, s>>>(g->nbr.geo, g->ctr.geo, d_meta);
+  PS_LAUNCH(PS_KID_EPILOGUE, s, k_query_epilogue<<<1, 32, 0, s>>>(g->nbr.geo, g->ctr.geo, d_meta));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

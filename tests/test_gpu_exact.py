@@ -30,11 +30,12 @@ def _dev(*arrs):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
 
 
-def run_gpu(ps, xyz, t, d, ctr, nbr, dmin, bins, ks, per_central=False, r_cut=None, cell_scale=1.0, rdf=True):
+def run_gpu(ps, xyz, t, d, ctr, nbr, dmin, bins, ks, per_central=False, r_cut=None, cell_scale=1.0, rdf=True,
+            dense_min=0):
     X, T, D = _dev(xyz, t, d)
     r0, dr, nb = bins
     rc = r_cut if r_cut is not None else float(np.float32(r0 + nb * dr)) * (1 + 1e-6)
-    g = ps.Grid(X.shape[0], cell_scale).build(X, T, nbr, rc)
+    g = ps.Grid(X.shape[0], cell_scale, dense_min).build(X, T, nbr, rc)
     out = ps.spatstat(g, D, ctr, dmin, bins, ks, rdf=rdf, per_central=per_central)
     torch.cuda.synchronize()
     res = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
@@ -137,13 +138,26 @@ def test_duplicates_edges_and_below_range(ps, orc):
 
 
 def test_dense_cells_many_chunks_and_batches(ps, orc, spec):
-    # 120 ions/nm^3: ~1000 centrals per cell and ~26k staged candidates per cell
+    # 120 ions/nm^3: ~1000 centrals per cell and ~26k candidates per cell (several staged chunks)
     xyz, t, d = spec.cube(104, 20000, (20000 / 120.0) ** (1 / 3), (0.5, 0.5))
     bins = (0.0, 0.02, 100)
     ks = [1, 16]
-    g = run_gpu(ps, xyz, t, d, "all", "all", 0.0, bins, ks, per_central=True)
     r = orc.spatstat(xyz, t, d, "all", "all", 0.0, *bins, ks, per_central=True)
-    assert_same(g, r, ks, per_central=True)
+    for dense_min in (0, 64):
+        g = run_gpu(ps, xyz, t, d, "all", "all", 0.0, bins, ks, per_central=True, dense_min=dense_min)
+        assert_same(g, r, ks, per_central=True)
+
+
+@pytest.mark.parametrize("cell_scale,dense_min", [(1.0, 0), (1.0, 40), (0.5, 0), (0.5, 8), (0.7, 0), (1.3, 1)])
+def test_kernel_variants_stencils(ps, orc, spec, cell_scale, dense_min):
+    """27- and 125-cell stencils, warp kernel alone and with the CTA kernel taking the dense cells."""
+    xyz, t, d = spec.cube(111, 12000, 7.5, (0.7, 0.2, 0.1))
+    bins = (0.0, 0.02, 80)
+    for ctr, nbr, dmin, ks in [("all", "all", 0.5, [1, 3, 12]), ([1], [1, 2], 0.0, [2]), ([0], "all", 1.0, [32])]:
+        g = run_gpu(ps, xyz, t, d, ctr, nbr, dmin, bins, ks, per_central=True, cell_scale=cell_scale,
+                    dense_min=dense_min)
+        r = orc.spatstat(xyz, t, d, ctr, nbr, dmin, *bins, ks, per_central=True)
+        assert_same(g, r, ks, per_central=True)
 
 
 def test_coarse_cells_cell_scale(ps, orc, spec):
