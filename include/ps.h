@@ -180,6 +180,33 @@ PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
                 uint64_t* d_hist, uint64_t* d_meta, void* stream);
 
 /*
+ * Allocation-free ps_build_grid + ps_spatstat.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * while they run the statistics, e.g. code running under CUDA stream capture
+ * (the runtime refuses allocations inside a capture) or acquisition loops that
+ * reserve all device memory up front and cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.
+ *   - Scratch is one file-scope device array sized for PS_STATIC_MAX_IONS
+ *     ions (about 15 MB), held on every GPU that uses the library until the
+ *     process exits.  No cudaMalloc, cudaFree or other allocating routine is
+ *     called.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - n > PS_STATIC_MAX_IONS returns PS_ERR_CAPACITY with nothing enqueued.
+ *   - Every call on a device shares the one array, which keeps the last call's
+ *     contents (each call clears what must start at zero).  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race and give
+ *     wrong results: serialise them.
+ *   - Cells of edge >= r_cut (the 27-cell search); arguments and outputs as
+ *     in ps_grid_build and ps_spatstat.
+ */
+#define PS_STATIC_MAX_IONS 262144
+PS_API int ps_spatstat_static(const float* xyz, const uint8_t* type, const float* dsrf, int64_t n,
+                              const uint64_t nbr_mask[4], float r_cut, const uint64_t ctr_mask[4], float dsrf_min,
+                              ps_bins bins, const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn,
+                              uint64_t* d_meta, float* d_kth, uint32_t* d_nwithin, void* stream);
+
+/*
  * Launch accounting and per-kernel timing (no counterpart in the paper; the
  * paper reports wall-clock per task).
  *   ps_launch_count   kernels this library has launched in this process.

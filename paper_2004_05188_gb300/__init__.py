@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libps.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "ps.h")
 
 PS_OK = 0
+STATIC_MAX_IONS = 262144
 STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_INVALID_INPUT", 3: "PS_ERR_OOM", 4: "PS_ERR_CUDA",
           5: "PS_ERR_TIMEOUT", 6: "PS_ERR_UNSUPPORTED", 7: "PS_ERR_CAPACITY"}
 K_MAX = 32
@@ -106,6 +107,7 @@ def lib():
     L.ps_spatstat.argtypes = [P, P, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_knn_hist.argtypes = [P, P, P, f32, u32, Bins, P, P, P, P]
     L.ps_rdf_hist.argtypes = [P, P, P, f32, Bins, P, P, P]
+    L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
     L.ps_prof_read.argtypes = [u32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
