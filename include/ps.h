@@ -180,6 +180,34 @@ PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
                 uint64_t* d_hist, uint64_t* d_meta, void* stream);
 
 /*
+ * Gaussian-smoothed RDF and its adjoint (the differentiable form).  The paper
+ * bins with rectangular transfer functions (Methods, "Descriptive, two-point
+ * spatial statistics, and clustering"); here each pair's distance is smoothed
+ * by a Gaussian of width sigma and integrated over every bin:
+ *   u_ij = scale * |x_j - x_i|   (float32 coordinates; pairs j != i, j in the
+ *                                  grid's neighbour set, i central as above)
+ *   h[b] = sum over pairs with u_ij < stop + 6 sigma of
+ *          Phi((e_{b+1} - u_ij)/sigma) - Phi((e_b - u_ij)/sigma),  e_b = r0 + b*dr
+ * ps_rdf_soft_fwd writes float32 h[n_bins] (d_h, device).
+ * ps_rdf_soft_bwd takes d_dLdh = dL/dh (float32 [n_bins], device) and writes
+ *   d_grad_xyz  float32 [n][3]: dL/dx for every ion of the grid's cloud
+ *               (zero for ions in no pair), overwritten
+ *   d_grad_scale float32 [1]: dL/dscale
+ * Pairs are recomputed in the adjoint, never stored.  The grid must have been
+ * built with r_cut * scale >= stop + 6 sigma (PS_ERR_INVALID_ARG otherwise) and
+ * must be rebuilt when the positions change.  The central set is chosen by
+ * d_srf at scale 1 and does not depend on scale.  Accuracy: float32 arithmetic
+ * on a fine grid of width <= sigma/40 with a second-order expansion per pair
+ * (relative error ~1e-6 of h and of the gradient).  Device-side input errors
+ * are reported by ps_grid_get_info.
+ */
+PS_API int ps_rdf_soft_fwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma,
+                           float scale, ps_bins bins, float* d_h, void* stream);
+PS_API int ps_rdf_soft_bwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma,
+                           float scale, ps_bins bins, const float* d_dLdh, float* d_grad_xyz, float* d_grad_scale,
+                           void* stream);
+
+/*
  * Allocation-free ps_build_grid + ps_spatstat.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * while they run the statistics, e.g. code running under CUDA stream capture

@@ -107,6 +107,8 @@ def lib():
     L.ps_spatstat.argtypes = [P, P, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_knn_hist.argtypes = [P, P, P, f32, u32, Bins, P, P, P, P]
     L.ps_rdf_hist.argtypes = [P, P, P, f32, Bins, P, P, P]
+    L.ps_rdf_soft_fwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P]
+    L.ps_rdf_soft_bwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
@@ -294,3 +296,80 @@ def rdf_hist(grid: Grid, dsrf, ctr_types, dsrf_min: float, bins, stream=None):
     _check(lib().ps_rdf_hist(grid.handle, _ptr(dsrf), mp, float(dsrf_min), Bins(r0, dr, nb), _ptr(h), _ptr(meta),
                              _stream(stream)))
     return h, meta
+
+
+def soft_rdf_fwd(grid: Grid, dsrf, ctr_types, dsrf_min: float, sigma: float, scale: float, bins, out=None,
+                 stream=None):
+    """Gaussian-smoothed RDF h[n_bins] (float32 CUDA tensor), ps_rdf_soft_fwd."""
+    import torch
+
+    r0, dr, nb = bins
+    h = out if out is not None else torch.empty(nb, dtype=torch.float32, device=grid._refs[0].device)
+    m, mp = _mask_ptr(ctr_types)
+    _check(lib().ps_rdf_soft_fwd(grid.handle, _ptr(dsrf), mp, float(dsrf_min), float(sigma), float(scale),
+                                 Bins(r0, dr, nb), _ptr(h), _stream(stream)))
+    return h
+
+
+def soft_rdf_bwd(grid: Grid, dsrf, ctr_types, dsrf_min: float, sigma: float, scale: float, bins, dLdh,
+                 grad_xyz=None, grad_scale=None, stream=None):
+    """Adjoint of soft_rdf_fwd (ps_rdf_soft_bwd): returns (dL/dxyz [n, 3], dL/dscale [1])."""
+    import torch
+
+    r0, dr, nb = bins
+    dev = grid._refs[0].device
+    dLdh = dLdh.contiguous().to(dtype=torch.float32)
+    gx = grad_xyz if grad_xyz is not None else torch.empty((grid.n, 3), dtype=torch.float32, device=dev)
+    gs = grad_scale if grad_scale is not None else torch.empty(1, dtype=torch.float32, device=dev)
+    m, mp = _mask_ptr(ctr_types)
+    _check(lib().ps_rdf_soft_bwd(grid.handle, _ptr(dsrf), mp, float(dsrf_min), float(sigma), float(scale),
+                                 Bins(r0, dr, nb), _ptr(dLdh), _ptr(gx), _ptr(gs), _stream(stream)))
+    return gx, gs
+
+
+def soft_r_cut(bins, sigma: float, scale: float) -> float:
+    """Grid cutoff (unscaled nm) that covers every pair of the smoothed RDF."""
+    r0, dr, nb = bins
+    return (r0 + nb * dr + 6.0 * sigma) / scale * (1.0 + 1e-5)
+
+
+def _soft_function():
+    import torch
+
+    class SoftRDF(torch.autograd.Function):
+        """h = SoftRDF.apply(xyz, scale, type, dsrf, nbr_types, ctr_types, dsrf_min, sigma, bins).
+
+        xyz: float32 CUDA [n, 3]; scale: 0-d or 1-element float tensor (its value is read on the host).
+        Forward builds the cell grid for the current positions and runs ps_rdf_soft_fwd; backward
+        reuses that grid and runs ps_rdf_soft_bwd (pairs recomputed).  Gradients flow to xyz and scale.
+        """
+
+        @staticmethod
+        def forward(ctx, xyz, scale, type_, dsrf, nbr_types, ctr_types, dsrf_min, sigma, bins):
+            s = float(scale.detach().reshape(-1)[0].item())
+            xyz_c = xyz.detach().contiguous()
+            g = Grid(xyz_c.shape[0]).build(xyz_c, type_, nbr_types, soft_r_cut(bins, sigma, s))
+            h = soft_rdf_fwd(g, dsrf, ctr_types, dsrf_min, sigma, s, bins)
+            ctx.grid, ctx.args = g, (dsrf, ctr_types, dsrf_min, sigma, s, bins)
+            ctx.scale_shape, ctx.scale_dev = scale.shape, scale.device
+            return h
+
+        @staticmethod
+        def backward(ctx, grad_h):
+            dsrf, ctr_types, dsrf_min, sigma, s, bins = ctx.args
+            gx, gs = soft_rdf_bwd(ctx.grid, dsrf, ctr_types, dsrf_min, sigma, s, bins, grad_h)
+            ctx.grid = None
+            return gx, gs.reshape(ctx.scale_shape).to(ctx.scale_dev), None, None, None, None, None, None, None
+
+    return SoftRDF
+
+
+_SoftRDF = None
+
+
+def soft_rdf(xyz, scale, type_, dsrf, nbr_types, ctr_types, dsrf_min, sigma, bins):
+    """Differentiable Gaussian-smoothed RDF (torch.autograd.Function over ps_rdf_soft_fwd/bwd)."""
+    global _SoftRDF
+    if _SoftRDF is None:
+        _SoftRDF = _soft_function()
+    return _SoftRDF.apply(xyz, scale, type_, dsrf, nbr_types, ctr_types, dsrf_min, sigma, bins)

@@ -101,7 +101,9 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   const size_t o_ncount = take(cc * 4), o_nstart = take((cc + 1) * 4), o_nrec = take(nm * 16);
   const size_t o_ccount = take(cc * 4), o_cstart = take((cc + 1) * 4), o_crec = take(nm * 16), o_cwork = take(cc * 4);
   g->item_cap = (uint32_t)(cc + nm / 32 + 2);
-  const size_t o_witem = take((size_t)g->item_cap * 8);
+  const size_t o_witem = take((size_t)g->item_cap * 8), o_nwitem = take((size_t)g->item_cap * 8);
+  const size_t o_sm0 = take(kSoftFineMax * 8), o_sm1 = take(kSoftFineMax * 8), o_sm2 = take(kSoftFineMax * 8);
+  const size_t o_sT = take(3 * kSoftFineMax * 4), o_sgs = take(8);
   const size_t o_part = take((size_t)g->scan_tiles_cap * 4), o_ngeo = take(sizeof(Geo)), o_cgeo = take(sizeof(Geo));
   void* base = nullptr;
   e = cudaMalloc(&base, off);
@@ -122,6 +124,12 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   g->ctr.rec = reinterpret_cast<float4*>(b + o_crec);
   g->ctr.work = reinterpret_cast<uint32_t*>(b + o_cwork);
   g->ctr.witem = reinterpret_cast<uint2*>(b + o_witem);
+  g->nbr_witem = reinterpret_cast<uint2*>(b + o_nwitem);
+  g->soft_m0 = reinterpret_cast<unsigned long long*>(b + o_sm0);
+  g->soft_m1 = reinterpret_cast<double*>(b + o_sm1);
+  g->soft_m2 = reinterpret_cast<double*>(b + o_sm2);
+  g->soft_T = reinterpret_cast<float*>(b + o_sT);
+  g->soft_gs = reinterpret_cast<double*>(b + o_sgs);
   g->ctr.geo = reinterpret_cast<Geo*>(b + o_cgeo);
   g->scan_part = reinterpret_cast<uint32_t*>(b + o_part);
   e = cudaMemset(g->nbr.geo, 0, sizeof(Geo));
@@ -182,10 +190,12 @@ int ps_build_grid(const float* xyz, const uint8_t* type, int64_t n, const uint64
 int ps_grid_get_info(ps_grid* g, ps_grid_info* info, void* stream) {
   if (!g || !info) return fail(PS_ERR_INVALID_ARG, "ps_grid_get_info: NULL argument");
   if (info->struct_size < sizeof(ps_grid_info)) return fail(PS_ERR_INVALID_ARG, "ps_grid_get_info: struct_size");
-  Geo h;
+  Geo h, hc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PS_CUDA(cudaMemcpyAsync(&h, g->nbr.geo, sizeof(Geo), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaMemcpyAsync(&hc, g->ctr.geo, sizeof(Geo), cudaMemcpyDeviceToHost, s));
   PS_CUDA(cudaStreamSynchronize(s));
+  if (h.status == 0) h.status = hc.status;
   for (int a = 0; a < 3; ++a) info->dims[a] = h.dims[a], info->origin[a] = h.origin[a];
   info->cell = h.h;
   info->n_nbr = h.n_sel;
@@ -219,6 +229,32 @@ int ps_spatstat(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float
     return fail(PS_ERR_INVALID_ARG, "ps_spatstat: the grid's r_cut is below the histogram stop");
   return run_query(g, dsrf, ctr_mask, dsrf_min, bins, ks, n_k, d_rdf, d_knn, d_meta, d_kth, d_nwithin,
                    static_cast<cudaStream_t>(stream));
+}
+
+static int check_soft(ps_grid* g, const uint64_t* ctr_mask, ps_bins bins, float dsrf_min) {
+  if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "smoothed RDF: grid is NULL or not built");
+  if (!ctr_mask) return fail(PS_ERR_INVALID_ARG, "smoothed RDF: ctr_mask is NULL");
+  if (std::isnan(dsrf_min)) return fail(PS_ERR_INVALID_ARG, "smoothed RDF: dsrf_min is NaN");
+  return check_bins(bins);
+}
+
+int ps_rdf_soft_fwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma,
+                    float scale, ps_bins bins, float* d_h, void* stream) {
+  int rc = check_soft(g, ctr_mask, bins, dsrf_min);
+  if (rc) return rc;
+  if (!d_h) return fail(PS_ERR_INVALID_ARG, "ps_rdf_soft_fwd: d_h is NULL");
+  return soft_forward(g, dsrf, ctr_mask, dsrf_min, sigma, scale, bins, d_h, static_cast<cudaStream_t>(stream));
+}
+
+int ps_rdf_soft_bwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma,
+                    float scale, ps_bins bins, const float* d_dLdh, float* d_grad_xyz, float* d_grad_scale,
+                    void* stream) {
+  int rc = check_soft(g, ctr_mask, bins, dsrf_min);
+  if (rc) return rc;
+  if (!d_dLdh || !d_grad_xyz || !d_grad_scale)
+    return fail(PS_ERR_INVALID_ARG, "ps_rdf_soft_bwd: d_dLdh/d_grad_xyz/d_grad_scale is NULL");
+  return soft_backward(g, dsrf, ctr_mask, dsrf_min, sigma, scale, bins, d_dLdh, d_grad_xyz, d_grad_scale,
+                       static_cast<cudaStream_t>(stream));
 }
 
 int ps_knn_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, uint32_t k, ps_bins bins,

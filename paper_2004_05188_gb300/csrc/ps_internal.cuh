@@ -10,6 +10,8 @@
 
 namespace ps {
 
+constexpr uint32_t kSoftFineMax = 8192;  // fine-grid bins of the smoothed RDF
+
 // ---------------------------------------------------------------------------
 // error reporting
 // ---------------------------------------------------------------------------
@@ -84,6 +86,13 @@ struct ps_grid {
   uint2* cr = nullptr;         // [n_max] (cell, rank) of selected ions
   uint32_t* scan_part = nullptr;  // [scan tiles]
   uint32_t scan_tiles_cap = 0;
+  // smoothed RDF scratch (fine grid of at most kSoftFineMax bins)
+  unsigned long long* soft_m0 = nullptr;
+  double* soft_m1 = nullptr;
+  double* soft_m2 = nullptr;
+  float* soft_T = nullptr;
+  double* soft_gs = nullptr;
+  uint2* nbr_witem = nullptr;  // [item_cap] warp items over the neighbour list (adjoint pass B)
   ps::CellList nbr;  // neighbour grid (geometry owner)
   ps::CellList ctr;  // central list, same geometry
   void* dev_block = nullptr;  // single allocation holding everything
@@ -115,6 +124,10 @@ __host__ __device__ inline float key2f(int32_t k) {
 // host-side builders shared between translation units
 int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cudaStream_t s);
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s);
+int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
+                 ps_bins bins, float* d_h, cudaStream_t s);
+int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
+                  ps_bins bins, const float* d_G, float* d_grad, float* d_grad_s, cudaStream_t s);
 
 struct Mask {
   uint64_t w[4];

@@ -1,0 +1,105 @@
+"""GPU parity of the Gaussian-smoothed RDF and its adjoint against the FP64 oracle.
+
+Tolerances (float32 arithmetic, fine-grid second-order expansion):
+  forward   ||h_gpu - h_ref|| <= 1e-5 ||h_ref||  and  |h_gpu - h_ref| <= 1e-5 max|h_ref| per bin
+  adjoint   ||g_gpu - g_ref|| <= 1e-4 ||g_ref||, per component <= 1e-4 max|g_ref|, dL/ds within 1e-4
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SIG = 0.05
+BINS = (0.0, 0.02, 100)
+
+
+@pytest.fixture(scope="module")
+def ps():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2004_05188_gb300 as ps
+
+    return ps
+
+
+def _dev(*a):
+    return [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
+
+
+def _run(ps, xyz, t, d, nbr, ctr, dmin, scale, G, cell_scale=1.0):
+    X, T, D = _dev(xyz, t, d)
+    g = ps.Grid(X.shape[0], cell_scale).build(X, T, nbr, ps.soft_r_cut(BINS, SIG, scale))
+    h = ps.soft_rdf_fwd(g, D, ctr, dmin, SIG, scale, BINS)
+    Gt = torch.from_numpy(G.astype(np.float32)).cuda()
+    gx, gs = ps.soft_rdf_bwd(g, D, ctr, dmin, SIG, scale, BINS, Gt)
+    torch.cuda.synchronize()
+    assert g.info()["status"] == 0
+    out = h.cpu().numpy().astype(np.float64), gx.cpu().numpy().astype(np.float64), float(gs.cpu()[0])
+    g.close()
+    return out
+
+
+def _check(orc, xyz, t, d, nbr, ctr, dmin, scale, G, h, gx, gs):
+    href = orc.soft_fwd(xyz, t, d, ctr, nbr, dmin, SIG, scale, *BINS)
+    gref, gsref = orc.soft_bwd(xyz, t, d, ctr, nbr, dmin, SIG, scale, *BINS, G)
+    assert np.linalg.norm(h - href) <= 1e-5 * np.linalg.norm(href)
+    assert np.max(np.abs(h - href)) <= 1e-5 * np.max(np.abs(href))
+    assert np.linalg.norm(gx - gref) <= 1e-4 * np.linalg.norm(gref)
+    assert np.max(np.abs(gx - gref)) <= 1e-4 * np.max(np.abs(gref))
+    assert abs(gs - gsref) <= 1e-4 * abs(gsref)
+    return href, gref, gsref
+
+
+@pytest.mark.parametrize("scale,cell_scale", [(1.0, 1.0), (0.93, 1.0), (1.07, 0.5)])
+def test_soft_forward_and_adjoint_vs_fp64(ps, orc, spec, scale, cell_scale):
+    xyz, t, d = spec.cube(201, 1500, 3.7, (0.7, 0.3))
+    G = np.random.default_rng(11).standard_normal(BINS[2])
+    h, gx, gs = _run(ps, xyz, t, d, "all", "all", 0.0, scale, G, cell_scale)
+    _check(orc, xyz, t, d, "all", "all", 0.0, scale, G, h, gx, gs)
+
+
+def test_soft_type_subsets_and_dsrf(ps, orc, spec):
+    xyz, t, d = spec.cube(202, 2000, 4.0, (0.6, 0.3, 0.1))
+    G = np.random.default_rng(12).standard_normal(BINS[2])
+    h, gx, gs = _run(ps, xyz, t, d, [0, 2], [1], 0.6, 1.0, G)
+    href, gref, _ = _check(orc, xyz, t, d, [0, 2], [1], 0.6, 1.0, G, h, gx, gs)
+    # ions in no pair have exactly zero gradient (non-central ions of type 1 are not neighbours)
+    cen = (t == 1) & (d >= 0.6)
+    lonely = (t == 1) & ~cen
+    assert np.all(gx[lonely] == 0.0)
+
+
+def test_soft_identities_at_scale(ps, spec):
+    """Translation invariance and the scaling identity on a 2e5-ion cylinder (any size)."""
+    xyz, t, d = spec.cylinder_small()
+    G = np.random.default_rng(13).standard_normal(BINS[2])
+    h, gx, gs = _run(ps, xyz, t, d, "all", "all", 2.3, 1.0, G)
+    tot = np.abs(gx).sum()
+    assert np.all(np.abs(gx.sum(0)) <= 1e-4 * tot)
+    euler = float((xyz.astype(np.float64) * gx).sum())
+    assert abs(gs - euler) <= 1e-4 * abs(gs)
+    assert h.min() >= 0 and h.sum() > 0
+
+
+def test_autograd_function_matches_oracle(ps, orc, spec):
+    xyz, t, d = spec.cube(203, 1200, 3.4, (1.0,))
+    X = torch.from_numpy(xyz).cuda().requires_grad_(True)
+    T, D = _dev(t, d)
+    s = torch.tensor(1.02, dtype=torch.float32, device="cuda", requires_grad=True)
+    target = torch.linspace(0, 1, BINS[2], device="cuda")
+    h = ps.soft_rdf(X, s, T, D, "all", "all", 0.0, SIG, BINS)
+    loss = ((h / h.sum() - target / target.sum()) ** 2).sum()
+    loss.backward()
+    # the upstream gradient dL/dh, computed by torch on the same h
+    hh = h.detach().clone().requires_grad_(True)
+    l2 = ((hh / hh.sum() - target / target.sum()) ** 2).sum()
+    (Gh,) = torch.autograd.grad(l2, [hh])
+    gref, gsref = orc.soft_bwd(xyz, t, d, "all", "all", 0.0, SIG, 1.02, *BINS, Gh.cpu().numpy().astype(np.float64))
+    gx = X.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gx - gref) <= 1e-4 * np.linalg.norm(gref)
+    assert abs(float(s.grad) - gsref) <= 1e-4 * abs(gsref)
