@@ -215,6 +215,86 @@ def algorithmic_bytes(kid: str, st: dict) -> float:
     return tot
 
 
+def measure_soft(args, dev):
+    """The differentiable form on the 1e7-ion needle: forward, loss, adjoint, against the plain exact RDF.
+
+    All types central and neighbour, d_srf >= 2.3 nm (= stop + 6 sigma: full ROIs), sigma = 0.05 nm,
+    r = [0, 0.02, 2] nm; the target g* comes from a copy of the cloud with every coordinate
+    perturbed by N(0, 0.02 nm) (seed 1)."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+    from paper_2004_05188_gb300 import specimen
+
+    p = specimen.needle_10m_params()
+    xyz, t, d = specimen.needle(p)
+    N = xyz.shape[0]
+    bins, sigma, dmin = (0.0, 0.02, 100), 0.05, 2.3
+    X = torch.from_numpy(xyz).to(dev)
+    T = torch.from_numpy(t).to(dev)
+    D = torch.from_numpy(d).to(dev)
+    pert = (xyz + np.random.default_rng(1).normal(0.0, 0.02, xyz.shape)).astype(np.float32)
+    Xp = torch.from_numpy(pert).to(dev)
+    rc = ps.soft_r_cut(bins, sigma, 1.0)
+    g = ps.Grid(N)
+    gp = ps.Grid(N)
+    # normalisation at fixed density: g_b = h_b / (N_c rho V_b)
+    vol = specimen.frustum_volume(p.r_top, math.degrees(p.half_angle), p.height)
+    e = np.arange(bins[2] + 1) * bins[1]
+    shell = torch.tensor(4.0 / 3.0 * np.pi * (e[1:] ** 3 - e[:-1] ** 3), dtype=torch.float32, device=dev)
+    rho = N / vol
+    gp.build(Xp, T, "all", rc)
+    h_star = ps.soft_rdf_fwd(gp, D, "all", dmin, sigma, 1.0, bins)
+    n_c = float(ps.spatstat(g.build(X, T, "all", rc), D, "all", dmin, bins, [], rdf=True)["meta"][0].item())
+    g_star = h_star / (n_c * rho * shell)
+    plain_out = dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
+                     meta=torch.empty(ps.META_HEAD, dtype=torch.int64, device=dev))
+
+    def fwd():
+        g.build(X, T, "all", rc)
+        return ps.soft_rdf_fwd(g, D, "all", dmin, sigma, 1.0, bins)
+
+    def loss_grad(h):
+        gg = h / (n_c * rho * shell)
+        return 2.0 * (gg - g_star) / (n_c * rho * shell)
+
+    def bwd(G):
+        return ps.soft_rdf_bwd(g, D, "all", dmin, sigma, 1.0, bins, G)
+
+    def plain():
+        g.build(X, T, "all", 2.0)
+        ps.spatstat(g, D, "all", dmin, bins, [], rdf=True, out=plain_out, check=False)
+
+    for _ in range(2):
+        G = loss_grad(fwd())
+        bwd(G)
+        plain()
+    torch.cuda.synchronize()
+    reps = 3
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    for r in range(reps):
+        ev[r][0].record()
+        h = fwd()
+        G = loss_grad(h)
+        ev[r][1].record()
+        bwd(G)
+        ev[r][2].record()
+        plain()
+        ev[r][3].record()
+    torch.cuda.synchronize()
+    f_ms = sum(ev[r][0].elapsed_time(ev[r][1]) for r in range(reps)) / reps
+    b_ms = sum(ev[r][1].elapsed_time(ev[r][2]) for r in range(reps)) / reps
+    p_ms = sum(ev[r][2].elapsed_time(ev[r][3]) for r in range(reps)) / reps
+    n_pairs = int(plain_out["meta"][1].item())
+    g.close()
+    gp.close()
+    return {"workload": f"needle {N} ions (1e7 target), all-all, sigma=0.05 nm, r=[0,0.02,2] nm, d_srf>=2.3 nm",
+            "n_central": int(n_c), "fwd_ms": f_ms, "bwd_ms": b_ms, "fwd_bwd_ms": f_ms + b_ms,
+            "plain_exact_rdf_ms": p_ms, "fwd_bwd_over_plain": (f_ms + b_ms) / p_ms,
+            "plain_pairs_per_s": n_pairs / (p_ms * 1e-3), "reps": reps,
+            "timing": "CUDA events, eager, grid build included in fwd and plain"}
+
+
 def run_gpu(args, wl_name, wl):
     import torch
 
@@ -402,6 +482,10 @@ def run_gpu(args, wl_name, wl):
                 "time_share": shares[dom] / max(1e-12, sum(shares.values())),
                 "shares": {k: round(v / max(1e-12, sum(shares.values())), 4) for k, v in shares.items()}}
 
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {"soft": measure_soft(args, dev)}
+
     # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -429,7 +513,7 @@ def run_gpu(args, wl_name, wl):
             "neighbour_pairs_per_s": tot_p * args.steps / (T_ms * 1e-3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clocks, "wall_s_timed_loop": wall,
-            "cuda_graph": graph is not None,
+            "cuda_graph": graph is not None, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -449,6 +533,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--no-forms", action="store_true", help="skip the smoothed-RDF and batched measurements")
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
     args = ap.parse_args()

@@ -103,3 +103,39 @@ def test_autograd_function_matches_oracle(ps, orc, spec):
     gx = X.grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gx - gref) <= 1e-4 * np.linalg.norm(gref)
     assert abs(float(s.grad) - gsref) <= 1e-4 * abs(gsref)
+
+
+def test_soft_gradient_vs_fp64_finite_differences_on_needle_subset(ps, orc, spec):
+    """2,000 ions of the 1e7-ion needle (the ions nearest the axis in a 3.6 nm slab at mid height):
+    the GPU adjoint against FP64 central differences of the oracle forward."""
+    p = spec.needle_10m_params()
+    counts = spec.needle_plan(p)
+    k0 = counts.shape[0] // 2
+    n = int(counts[k0:k0 + 9].sum())
+    xyz = np.empty((n, 3), np.float32)
+    t = np.empty(n, np.uint8)
+    d = np.empty(n, np.float32)
+    spec.needle_fill(p, k0, k0 + 9, counts, xyz.ctypes.data, t.ctypes.data, d.ctypes.data)
+    sel = np.sort(np.argsort(np.hypot(xyz[:, 0], xyz[:, 1]))[:2000])
+    xyz, t, d = xyz[sel], t[sel], d[sel]
+    d = np.full_like(d, 10.0)  # every ion of the subset is central
+    G = np.random.default_rng(14).standard_normal(BINS[2])
+    h, gx, gs = _run(ps, xyz, t, d, "all", "all", 0.0, 1.0, G)
+    gref, gsref = orc.soft_bwd(xyz, t, d, "all", "all", 0.0, SIG, 1.0, *BINS, G)
+    assert np.linalg.norm(gx - gref) <= 1e-4 * np.linalg.norm(gref)
+
+    def loss(x, s=1.0):
+        return float(G @ orc.soft_fwd(x, t, d, "all", "all", 0.0, SIG, s, *BINS))
+
+    eps = 2.0**-13  # |x|, |y| < 4 nm here: x +- eps is exact in float32
+    gmax = np.abs(gref).max()
+    for i, a in [(17, 0), (1000, 1), (1999, 0)]:
+        assert abs(xyz[i, a]) < 4.0
+        xp, xm = xyz.copy(), xyz.copy()
+        xp[i, a] += np.float32(eps)
+        xm[i, a] -= np.float32(eps)
+        fd = (loss(xp) - loss(xm)) / (2 * eps)
+        assert abs(gx[i, a] - fd) <= 1e-4 * gmax, (i, a, gx[i, a], fd)
+    es = 1e-5
+    fds = (loss(xyz, 1 + es) - loss(xyz, 1 - es)) / (2 * es)
+    assert abs(gs - fds) <= 1e-4 * abs(fds)
