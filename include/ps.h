@@ -180,6 +180,58 @@ PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
                 uint64_t* d_hist, uint64_t* d_meta, void* stream);
 
 /*
+ * Batched sweeps over many ROIs in one persistent launch.  The paper's batch
+ * queue evaluates an a-priori list of (statistic, type combination, dataset)
+ * tasks from one neighbour search per ROI (Suppl. "Customized user defined
+ * batch processing queues"); here every ROI is enumerated once at the largest
+ * r_max, and each sweep point is derived exactly: all k = 1..k_max from one
+ * top-k list, smaller r_max as prefixes of the histograms, d_srf thresholds
+ * as sums over d_srf classes, all type pairs from the same enumeration.
+ *
+ * ps_dataset: one ROI, device pointers (xyz float32 [n][3], type uint8 [n],
+ *   dsrf float32 [n] or NULL), n < 2^24 ions; arrays must stay valid while the
+ *   batch exists.
+ * ps_sweep: the histogram bins at the largest r_max (n_bins <= 512); rmax_bins
+ *   the r_max values as ascending bin counts (last = bins.n_bins); dsrf_min the
+ *   ascending d_srf thresholds; type pairs (ctr_mask, nbr_mask), at most two
+ *   distinct neighbour sets; k = 1..k_max; cell_scale as in ps_grid_opts.
+ *   Limit: n_pairs * n_dsrf * n_bins <= 16384.
+ * ps_batch_create allocates every grid and accumulator (synchronises).
+ * ps_batch_run enqueues the builds of all ROIs, the one persistent query
+ *   kernel and the expansion into d_out (uint64, ps_batch_out_len elements):
+ *   for each (ROI, pair, r_max, d_srf threshold) in that nesting order a record
+ *   rdf[n_bins] | knn[k_max][n_bins] | meta[PS_META_LEN(k_max)], identical to
+ *   ps_spatstat with the same parameters (entries past that r_max's bins are 0).
+ *   No host synchronisation: the sequence can be captured in a CUDA graph.
+ */
+typedef struct {
+  const float* xyz;
+  const uint8_t* type;
+  const float* dsrf;
+  int64_t n;
+} ps_dataset;
+
+typedef struct {
+  uint32_t struct_size;
+  ps_bins bins;
+  uint32_t n_rmax;
+  uint32_t rmax_bins[4];
+  uint32_t n_dsrf;
+  float dsrf_min[4];
+  uint32_t n_pairs;
+  uint64_t ctr_mask[4][4];
+  uint64_t nbr_mask[4][4];
+  uint32_t k_max;
+  float cell_scale;
+} ps_sweep;
+
+typedef struct ps_batch ps_batch;
+PS_API int ps_batch_create(const ps_dataset* datasets, int n_datasets, const ps_sweep* sweep, ps_batch** out);
+PS_API int ps_batch_run(ps_batch* b, uint64_t* d_out, void* stream);
+PS_API int64_t ps_batch_out_len(const ps_batch* b);
+PS_API int ps_batch_destroy(ps_batch* b);
+
+/*
  * Gaussian-smoothed RDF and its adjoint (the differentiable form).  The paper
  * bins with rectangular transfer functions (Methods, "Descriptive, two-point
  * spatial statistics, and clustering"); here each pair's distance is smoothed

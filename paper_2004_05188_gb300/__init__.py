@@ -77,6 +77,17 @@ class GridInfo(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class Dataset(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("type", ctypes.c_void_p), ("dsrf", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class Sweep(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("bins", Bins), ("n_rmax", ctypes.c_uint32),
+                ("rmax_bins", ctypes.c_uint32 * 4), ("n_dsrf", ctypes.c_uint32), ("dsrf_min", ctypes.c_float * 4),
+                ("n_pairs", ctypes.c_uint32), ("ctr_mask", (ctypes.c_uint64 * 4) * 4),
+                ("nbr_mask", (ctypes.c_uint64 * 4) * 4), ("k_max", ctypes.c_uint32), ("cell_scale", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -107,6 +118,11 @@ def lib():
     L.ps_spatstat.argtypes = [P, P, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_knn_hist.argtypes = [P, P, P, f32, u32, Bins, P, P, P, P]
     L.ps_rdf_hist.argtypes = [P, P, P, f32, Bins, P, P, P]
+    L.ps_batch_create.argtypes = [ctypes.POINTER(Dataset), ctypes.c_int, ctypes.POINTER(Sweep), ctypes.POINTER(P)]
+    L.ps_batch_run.argtypes = [P, P, P]
+    L.ps_batch_out_len.argtypes = [P]
+    L.ps_batch_out_len.restype = ctypes.c_int64
+    L.ps_batch_destroy.argtypes = [P]
     L.ps_rdf_soft_fwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P]
     L.ps_rdf_soft_bwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
@@ -373,3 +389,70 @@ def soft_rdf(xyz, scale, type_, dsrf, nbr_types, ctr_types, dsrf_min, sigma, bin
     if _SoftRDF is None:
         _SoftRDF = _soft_function()
     return _SoftRDF.apply(xyz, scale, type_, dsrf, nbr_types, ctr_types, dsrf_min, sigma, bins)
+
+
+class Batch:
+    """Batched sweeps over many ROIs (ps_batch_create / ps_batch_run).
+
+    datasets: list of (xyz, type, dsrf) CUDA tensors (dsrf may be None).
+    bins: (r0, dr, n_bins) at the largest r_max; rmax_bins: ascending bin counts (last = n_bins);
+    dsrf_min: ascending thresholds; pairs: list of (ctr_types, nbr_types); k_max: k = 1..k_max.
+    run() returns an int64 CUDA tensor [n_roi, n_pairs, n_rmax, n_dsrf, rec] with
+    rec = n_bins + k_max * n_bins + 4 + 2 * k_max (rdf | knn | meta, as ps_spatstat).
+    """
+
+    def __init__(self, datasets, bins, rmax_bins, dsrf_min, pairs, k_max, cell_scale=1.0):
+        self._refs = list(datasets)
+        ds = (Dataset * len(datasets))()
+        for i, (X, T, D) in enumerate(datasets):
+            _check_cloud(X, T, D)
+            ds[i] = Dataset(X.data_ptr(), T.data_ptr(), D.data_ptr() if D is not None else None, X.shape[0])
+        sw = Sweep()
+        sw.struct_size = ctypes.sizeof(Sweep)
+        sw.bins = Bins(*bins)
+        sw.n_rmax = len(rmax_bins)
+        for i, r in enumerate(rmax_bins):
+            sw.rmax_bins[i] = int(r)
+        sw.n_dsrf = len(dsrf_min)
+        for i, d in enumerate(dsrf_min):
+            sw.dsrf_min[i] = float(d)
+        sw.n_pairs = len(pairs)
+        for p, (c, n) in enumerate(pairs):
+            mc, mn = type_mask(c), type_mask(n)
+            for w in range(4):
+                sw.ctr_mask[p][w] = int(mc[w])
+                sw.nbr_mask[p][w] = int(mn[w])
+        sw.k_max = int(k_max)
+        sw.cell_scale = float(cell_scale)
+        h = ctypes.c_void_p()
+        _check(lib().ps_batch_create(ds, len(datasets), ctypes.byref(sw), ctypes.byref(h)))
+        self._h = h
+        self.shape = (len(datasets), len(pairs), len(rmax_bins), len(dsrf_min),
+                      bins[2] + k_max * bins[2] + META_HEAD + 2 * k_max)
+        self.bins, self.k_max = bins, k_max
+
+    def run(self, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.int64, device=self._refs[0][0].device)
+        assert out.numel() == lib().ps_batch_out_len(self._h)
+        _check(lib().ps_batch_run(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def split(self, rec):
+        """rec [..., rec_len] -> (rdf [..., n_bins], knn [..., k_max, n_bins], meta [..., 4 + 2 k_max])."""
+        nb, k = self.bins[2], self.k_max
+        return rec[..., :nb], rec[..., nb:nb + k * nb].reshape(*rec.shape[:-1], k, nb), rec[..., nb + k * nb:]
+
+    def close(self):
+        if self._h:
+            _check(lib().ps_batch_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.ps_batch_destroy(self._h)
+        except Exception:
+            pass

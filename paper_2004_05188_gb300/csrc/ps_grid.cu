@@ -424,16 +424,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
   }
 }
 
-// Scatter the selected ions to their sorted slot.
+// Scatter the selected ions to their sorted slot.  The record's 4th word is the
+// ion index, or (index << 8 | type) when `type` is given (clouds of < 2^24 ions).
 __global__ void __launch_bounds__(kThreads) k_scatter(const float* __restrict__ xyz, const uint32_t* __restrict__ sel,
                                                       const uint2* __restrict__ cr, const uint32_t* __restrict__ start,
-                                                      const Geo* __restrict__ cnt, float4* __restrict__ rec) {
+                                                      const Geo* __restrict__ cnt, float4* __restrict__ rec,
+                                                      const uint8_t* __restrict__ type) {
   const uint32_t ns = cnt->n_sel;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
     const uint32_t i = sel[s];
     const uint2 c = cr[s];
     const int64_t b = 3 * (int64_t)i;
-    rec[start[c.x] + c.y] = make_float4(xyz[b], xyz[b + 1], xyz[b + 2], __uint_as_float(i));
+    const uint32_t w = type ? ((i << 8) | type[i]) : i;
+    rec[start[c.x] + c.y] = make_float4(xyz[b], xyz[b + 1], xyz[b + 2], __uint_as_float(w));
   }
 }
 
@@ -467,7 +470,8 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
   int rc = scan_cells(g, g->nbr, geo, false, s);
   if (rc) return rc;
   PS_LAUNCH(PS_KID_SCATTER, s,
-            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec));
+            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec,
+                                                             g->pack_type ? g->type : nullptr));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -486,7 +490,8 @@ int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
   int rc = scan_cells(g, g->ctr, g->ctr.geo, true, s);
   if (rc) return rc;
   PS_LAUNCH(PS_KID_SCATTER, s,
-            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec));
+            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec,
+                                                             g->pack_type ? g->type : nullptr));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

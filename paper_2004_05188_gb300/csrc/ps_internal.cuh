@@ -82,6 +82,7 @@ struct ps_grid {
   uint32_t dense_min = 0xFFFFFFFFu;  // cells with at least this many centrals go to the CTA-staged kernel
   uint32_t item_cap = 0;       // capacity of the warp item list
   int stencil = 1;             // neighbour cells searched on each side (1: cell >= r_cut, 2: cell >= r_cut/2)
+  bool pack_type = false;      // records carry (index << 8 | type) instead of the index (batched sweeps)
   uint32_t* sel = nullptr;     // [n_max] selected ion indices
   uint2* cr = nullptr;         // [n_max] (cell, rank) of selected ions
   uint32_t* scan_part = nullptr;  // [scan tiles]
