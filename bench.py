@@ -295,6 +295,88 @@ def measure_soft(args, dev):
             "timing": "CUDA events, eager, grid build included in fwd and plain"}
 
 
+def measure_batched(args, dev):
+    """256 ROIs (needles and cylinders, log-uniform 1e4..1e7 ions), each with the sweep
+    k = 1..20, r_max in {1, 2, 3} nm (0.01 nm bins), d_srf >= {0, 1, 2} nm, type pairs
+    all-all, Sc-Sc, Al-Sc: one CUDA-graph replay of the batched path for all ROIs; and, on a
+    subset of 16 ROIs spread over the size range, the batched path against one plain exact
+    call per ROI and sweep point (27 calls per ROI, each with k = 1..20)."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+    from paper_2004_05188_gb300 import specimen
+
+    sizes = specimen.roi_sizes(args.batch_rois)
+    t0 = time.perf_counter()
+    host = [specimen.roi(i, n) for i, n in enumerate(sizes)]
+    gen_s = time.perf_counter() - t0
+    rois = [tuple(torch.from_numpy(a).to(dev) for a in r) for r in host]
+    n_ions = int(sum(r[0].shape[0] for r in rois))
+    del host
+    bins, rmax, dsrf = (0.0, 0.01, 300), [100, 200, 300], [0.0, 1.0, 2.0]
+    pairs, k_max = [("all", "all"), ([1], [1]), ([0], [1])], 20
+
+    def graph_time(b, reps=1):
+        out = torch.empty(b.shape, dtype=torch.int64, device=dev)
+        b.run(out)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.run(out)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    b = ps.Batch(rois, bins, rmax, dsrf, pairs, k_max, args.batch_cell_scale)
+    all_ms, out = graph_time(b)
+    meta = out[..., -(4 + 2 * k_max):]
+    n_central_all = int(meta[:, 0, -1, 0, 0].sum().item())  # all-all, r_max 3, d_srf >= 0
+    b.close()
+    del out
+
+    sub = list(range(0, len(rois), max(1, len(rois) // 16)))[:16]
+    bs = ps.Batch([rois[i] for i in sub], bins, rmax, dsrf, pairs, k_max, args.batch_cell_scale)
+    sub_ms, _ = graph_time(bs)
+    bs.close()
+    ks = list(range(1, k_max + 1))
+    grids = {i: ps.Grid(rois[i][0].shape[0], args.batch_cell_scale) for i in sub}
+
+    def plain_all():
+        for i in sub:
+            X, T, D = rois[i]
+            for ctr, nbr in pairs:
+                for nb in rmax:
+                    grids[i].build(X, T, nbr, nb * 0.01 * (1 + 1e-6))
+                    for dmin in dsrf:
+                        ps.spatstat(grids[i], D, ctr, dmin, (0.0, 0.01, nb), ks, check=False)
+
+    plain_all()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plain_all()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    for gd in grids.values():
+        gd.close()
+    return {"workload": f"{len(rois)} ROIs, {n_ions} ions (log-uniform 1e4..1e7), k=1..20, r_max {{1,2,3}} nm, "
+                        "d_srf {0,1,2} nm, pairs all-all/Sc-Sc/Al-Sc",
+            "sweep_points": len(rois) * 27, "batched_ms": all_ms,
+            "ion_queries_per_s": n_central_all / (all_ms * 1e-3),
+            "subset_rois": len(sub), "subset_batched_ms": sub_ms, "subset_plain_ms": plain_ms,
+            "plain_over_batched": plain_ms / sub_ms, "cell_scale": args.batch_cell_scale,
+            "host_generation_s": gen_s,
+            "timing": "CUDA events; batched = one CUDA-graph replay (grid builds + one persistent query "
+                      "kernel + expansion); plain = one eager ps_spatstat per ROI and sweep point"}
+
+
 def run_gpu(args, wl_name, wl):
     import torch
 
@@ -485,6 +567,8 @@ def run_gpu(args, wl_name, wl):
     forms = None
     if rank == 0 and not args.no_forms:
         forms = {"soft": measure_soft(args, dev)}
+        if args.batch_rois > 0:
+            forms["batched"] = measure_batched(args, dev)
 
     # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
@@ -534,6 +618,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-forms", action="store_true", help="skip the smoothed-RDF and batched measurements")
+    ap.add_argument("--batch-rois", type=int, default=256, help="ROIs of the batched measurement (0 skips it)")
+    ap.add_argument("--batch-cell-scale", type=float, default=1.0)
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
     args = ap.parse_args()

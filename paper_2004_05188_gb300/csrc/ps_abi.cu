@@ -80,7 +80,9 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   g->stencil = cell_scale >= 1.0f ? 1 : 2;
   g->block = block;
   if (opts && opts->struct_size >= sizeof(ps_grid_opts)) g->dense_min = opts->dense_min ? opts->dense_min : 0xFFFFFFFFu;
-  const int64_t cap0 = g->stencil == 2 ? g->n_max * 2 : g->n_max / 2;
+  // cells: a bounding-box grid at the cutoff needs ~n/100 cells for the clouds seen here; the
+  // capacity leaves a wide margin (the cell edge grows past it, results do not change)
+  const int64_t cap0 = g->stencil == 2 ? g->n_max : g->n_max / 8;
   const int64_t cap = cap0 > 65536 ? cap0 : 65536;
   g->cell_cap = (uint32_t)(cap < (int64_t)1 << 31 ? cap : (int64_t)1 << 31);
   g->scan_tiles_cap = (g->cell_cap + 4095) / 4096;

@@ -97,7 +97,7 @@ __device__ __forceinline__ uint32_t bbin(float d2, const float* sE, uint32_t nb,
 }
 
 template <int KMAX, int NL>
-__global__ void __launch_bounds__(256) k_batch_query(const BatchArgs a) {
+__global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ float s_hd[8][512];
@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(256) k_batch_query(const BatchArgs a) {
   __shared__ uint32_t s_rsrc[8][kBatchRuns], s_rpre[8][kBatchRuns + 1];
   __shared__ uint32_t s_chunk, s_roi;
   __shared__ unsigned long long s_bound;
+  __shared__ uint32_t s_tinfo[256];  // per type: bit l = in list l's neighbour set, bit 2 + p = in pair p's
 
   const uint32_t nb = a.n_bins, P = a.n_pairs, C = a.n_cls;
   float* sE = reinterpret_cast<float*>(smem);
@@ -117,6 +118,12 @@ __global__ void __launch_bounds__(256) k_batch_query(const BatchArgs a) {
     sE[b] = __double2float_rn(__dmul_rn(e, e));
   }
   for (uint32_t i = threadIdx.x; i < n_sh; i += blockDim.x) s_rdf[i] = 0;
+  for (uint32_t t = threadIdx.x; t < 256; t += blockDim.x) {
+    uint32_t v = 0;
+    for (uint32_t l = 0; l < (uint32_t)NL; ++l) v |= (mask_has(a.list_mask[l], t) ? 1u : 0u) << l;
+    for (uint32_t pp = 0; pp < P; ++pp) v |= (mask_has(a.nbr_mask[pp], t) ? 1u : 0u) << (2 + pp);
+    s_tinfo[t] = v;
+  }
   if (threadIdx.x == 0) s_bound = 0;
   __syncthreads();
   const float Emax = sE[nb], E0 = sE[0], r0f = (float)a.r0, inv_dr = (float)(1.0 / a.dr);
@@ -270,12 +277,11 @@ __global__ void __launch_bounds__(256) k_batch_query(const BatchArgs a) {
               const bool hit = d2v[e] < emax && qw != pw;
               uint32_t tag = 0;
               if (hit) {
-                const uint32_t tj = qw & 0xFFu;
+                const uint32_t ti = s_tinfo[qw & 0xFFu];
 #pragma unroll
                 for (int l = 0; l < NL; ++l)
-                  if (mask_has(a.list_mask[l], tj) && d2v[e] < top[l][KMAX - 1]) tk_insert(top[l], d2v[e]);
-                for (uint32_t pp = 0; pp < P; ++pp)
-                  if (((pmask >> pp) & 1u) && mask_has(a.nbr_mask[pp], tj)) tag |= 1u << pp;
+                  if (((ti >> l) & 1u) && d2v[e] < top[l][KMAX - 1]) tk_insert(top[l], d2v[e]);
+                tag = (ti >> 2) & pmask;
               }
               const bool rec = tag != 0;
               const uint32_t bal = __ballot_sync(0xffffffffu, rec);
@@ -598,12 +604,12 @@ int ps_batch_run(ps_batch* b, uint64_t* d_out, void* stream) {
   if (b->n_lists == 1)
     rc = k <= 8 ? launch_batch<8, 1>(b, a, smem, sms, st)
          : k <= 16 ? launch_batch<16, 1>(b, a, smem, sms, st)
-         : k <= 24 ? launch_batch<24, 1>(b, a, smem, sms, st)
+         : k <= 20 ? launch_batch<20, 1>(b, a, smem, sms, st)
                    : launch_batch<32, 1>(b, a, smem, sms, st);
   else
     rc = k <= 8 ? launch_batch<8, 2>(b, a, smem, sms, st)
          : k <= 16 ? launch_batch<16, 2>(b, a, smem, sms, st)
-         : k <= 24 ? launch_batch<24, 2>(b, a, smem, sms, st)
+         : k <= 20 ? launch_batch<20, 2>(b, a, smem, sms, st)
                    : launch_batch<32, 2>(b, a, smem, sms, st);
   if (rc) return rc;
   const uint32_t n_out = n_roi * s.n_pairs * s.n_rmax * s.n_dsrf;

@@ -8,7 +8,7 @@
 // reserve all device memory at start-up and must not block on the implicit
 // device synchronisation of cudaMalloc/cudaFree in the loop.
 //
-// The array is sized for PS_STATIC_MAX_IONS ions (about 15 MB) and every
+// The array is sized for PS_STATIC_MAX_IONS ions (about 13 MB) and every
 // process that loads libps holds it on each GPU it uses until exit.
 #include <mutex>
 
@@ -25,7 +25,7 @@ namespace {
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t kN = PS_STATIC_MAX_IONS;
-constexpr size_t kCells = kN / 2 > 65536 ? kN / 2 : 65536;  // same cell capacity rule as ps_grid_create
+constexpr size_t kCells = kN / 8 > 65536 ? kN / 8 : 65536;  // same cell capacity rule as ps_grid_create
 constexpr size_t kTiles = (kCells + 4095) / 4096;
 constexpr size_t kItems = kCells + kN / 32 + 2;
 
