@@ -41,6 +41,10 @@ WORKLOADS = {
         desc="needle 8.07e6 ions (r_tip 20 nm, 10 deg, h 100 nm, 30/nm^3, Al3Sc precipitates); Sc-Sc + Si-Si; "
              "kNN k=1,5,10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
         combos=[("Sc-Sc", [1], [1]), ("Si-Si", [2], [2])], ks=[1, 5, 10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
+    "needle2g": dict(
+        desc="needle 2e9 ions (r_tip 40 nm, 15 deg, h 812.6 nm, 30/nm^3, Al3Sc precipitates); all-all + Sc-Sc; "
+             "kNN k=10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
+        combos=[("all-all", "all", "all"), ("Sc-Sc", [1], [1])], ks=[10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
     "cylinder200k": dict(
         desc="Poisson cylinder 2e5 ions (R 10 nm, H 15.9 nm, 40/nm^3); all-all; kNN k=1 + RDF r=[0,0.01,2] nm; "
              "d_srf>=1 nm",
@@ -55,6 +59,8 @@ def make_cloud(name: str, seed_offset: int = 0):
         return specimen.needle(specimen.needle_8m_params(seed=2 + seed_offset))
     if name == "cylinder200k":
         return specimen.cylinder_small(seed=1 + seed_offset)
+    if name == "needle2g":
+        return specimen.needle(specimen.needle_2g_params(seed=5 + seed_offset))
     raise ValueError(name)
 
 

@@ -195,7 +195,7 @@ PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
  *   the r_max values as ascending bin counts (last = bins.n_bins); dsrf_min the
  *   ascending d_srf thresholds; type pairs (ctr_mask, nbr_mask), at most two
  *   distinct neighbour sets; k = 1..k_max; cell_scale as in ps_grid_opts.
- *   Limit: n_pairs * n_dsrf * n_bins <= 16384.
+ *   Limit: n_pairs * n_dsrf * n_bins <= 8192.
  * ps_batch_create allocates every grid and accumulator (synchronises).
  * ps_batch_run enqueues the builds of all ROIs, the one persistent query
  *   kernel and the expansion into d_out (uint64, ps_batch_out_len elements):

@@ -104,27 +104,26 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
   __shared__ uint32_t s_ht[8][512];
   __shared__ uint32_t s_rsrc[8][kBatchRuns], s_rpre[8][kBatchRuns + 1];
   __shared__ uint32_t s_chunk, s_roi;
-  __shared__ unsigned long long s_bound;
   __shared__ uint32_t s_tinfo[256];  // per type: bit l = in list l's neighbour set, bit 2 + p = in pair p's
 
   const uint32_t nb = a.n_bins, P = a.n_pairs, C = a.n_cls;
+  // 64-bit pair counters (a CTA may count more than 2^32 pairs of one ROI), 32-bit central counts
   float* sE = reinterpret_cast<float*>(smem);
-  uint32_t* s_rdf = reinterpret_cast<uint32_t*>(smem + ((nb + 1) * 4 + 15) / 16 * 16);  // [P][C][nb]
-  uint32_t* s_below = s_rdf + P * C * nb;                                                  // [P][C]
-  uint32_t* s_nc = s_below + P * C;                                                        // [P][C]
-  const uint32_t n_sh = P * C * nb + 2 * P * C;
+  unsigned long long* s_rdf = reinterpret_cast<unsigned long long*>(smem + ((nb + 1) * 4 + 15) / 16 * 16);  // [P][C][nb+1]
+  uint32_t* s_nc = reinterpret_cast<uint32_t*>(s_rdf + P * C * (nb + 1));                                   // [P][C]
+  const uint32_t n_rdf = P * C * (nb + 1);  // per (p, c): nb bins then the below-range count
   for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
     const double e = __dadd_rn(a.r0, __dmul_rn((double)b, a.dr));
     sE[b] = __double2float_rn(__dmul_rn(e, e));
   }
-  for (uint32_t i = threadIdx.x; i < n_sh; i += blockDim.x) s_rdf[i] = 0;
+  for (uint32_t i = threadIdx.x; i < n_rdf; i += blockDim.x) s_rdf[i] = 0ull;
+  for (uint32_t i = threadIdx.x; i < P * C; i += blockDim.x) s_nc[i] = 0;
   for (uint32_t t = threadIdx.x; t < 256; t += blockDim.x) {
     uint32_t v = 0;
     for (uint32_t l = 0; l < (uint32_t)NL; ++l) v |= (mask_has(a.list_mask[l], t) ? 1u : 0u) << l;
     for (uint32_t pp = 0; pp < P; ++pp) v |= (mask_has(a.nbr_mask[pp], t) ? 1u : 0u) << (2 + pp);
     s_tinfo[t] = v;
   }
-  if (threadIdx.x == 0) s_bound = 0;
   __syncthreads();
   const float Emax = sE[nb], E0 = sE[0], r0f = (float)a.r0, inv_dr = (float)(1.0 / a.dr);
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -135,22 +134,17 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
   auto flush = [&](int roi) {
     __syncthreads();
     unsigned long long* A = a.acc + (size_t)roi * a.acc_len;
-    for (uint32_t i = threadIdx.x; i < n_sh; i += blockDim.x) {
-      const uint32_t v = s_rdf[i];
+    for (uint32_t i = threadIdx.x; i < n_rdf; i += blockDim.x) {
+      const unsigned long long v = s_rdf[i];
       if (!v) continue;
-      uint32_t off;
-      if (i < P * C * nb) {
-        const uint32_t pc = i / nb, b = i % nb;
-        off = pc * blk + b;
-      } else if (i < P * C * nb + P * C) {
-        off = (i - P * C * nb) * blk + nb;
-      } else {
-        off = (i - P * C * nb - P * C) * blk + nb + 1;
-      }
-      atomicAdd(&A[off], (unsigned long long)v);
-      s_rdf[i] = 0;
+      // rdf[b] at offset b of block pc, the below-range count at offset nb
+      atomicAdd(&A[(i / (nb + 1)) * blk + i % (nb + 1)], v);
+      s_rdf[i] = 0ull;
     }
-    if (threadIdx.x == 0) s_bound = 0;
+    for (uint32_t i = threadIdx.x; i < P * C; i += blockDim.x) {
+      if (s_nc[i]) atomicAdd(&A[i * blk + nb + 1], (unsigned long long)s_nc[i]);
+      s_nc[i] = 0;
+    }
     __syncthreads();
   };
 
@@ -215,12 +209,6 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
       }
       if (lane == 0) rpre[0] = 0;
       __syncwarp();
-      // shared RDF counters take at most 2^31 increments per flush; beyond that, global
-      unsigned long long old = 0;
-      const unsigned long long inc = (unsigned long long)cnt * ((unsigned long long)n_cand + 1) * P;
-      if (lane == 0) old = atomicAdd(&s_bound, inc);
-      old = __shfl_sync(0xffffffffu, old, 0);
-      const bool glob = old + inc >= (1ull << 31);
 
       // this lane's central: type, class, pair membership
       const bool valid = lane < cnt;
@@ -301,14 +289,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
             const uint32_t bn = below ? 0u : bbin(d2, sE, nb, r0f, inv_dr);
             for (uint32_t pp = 0; pp < P; ++pp) {
               if (!((tg >> pp) & 1u)) continue;
-              const uint32_t pc = pp * C + cc;
-              if (glob) {
-                atomicAdd(&A[pc * blk + (below ? nb : bn)], 1ull);
-              } else if (below) {
-                atomicAdd(&s_below[pc], 1u);
-              } else {
-                atomicAdd(&s_rdf[pc * nb + bn], 1u);
-              }
+              atomicAdd(&s_rdf[(pp * C + cc) * (nb + 1) + (below ? nb : bn)], 1ull);
             }
           }
           __syncwarp();
@@ -319,10 +300,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
         for (uint32_t pp = 0; pp < P; ++pp) {
           if (!((pmask >> pp) & 1u)) continue;
           const uint32_t pc = pp * C + cls;
-          if (glob)
-            atomicAdd(&A[pc * blk + nb + 1], 1ull);
-          else
-            atomicAdd(&s_nc[pc], 1u);
+          atomicAdd(&s_nc[pc], 1u);
           const uint32_t l = a.list_of[pp];
           for (uint32_t k = 0; k < a.k_max; ++k) {
             float D = INFINITY;
@@ -467,7 +445,7 @@ int ps_batch_create(const ps_dataset* ds, int n_ds, const ps_sweep* sw, ps_batch
     if (std::isnan(s.dsrf_min[q]) || (q && !(s.dsrf_min[q] > s.dsrf_min[q - 1])))
       return fail(PS_ERR_INVALID_ARG, "ps_batch_create: dsrf_min must ascend");
   const uint32_t smem_rdf = s.n_pairs * s.n_dsrf * s.bins.n_bins;
-  if (smem_rdf > 16384) return fail(PS_ERR_UNSUPPORTED, "ps_batch_create: pairs x thresholds x bins > 16384");
+  if (smem_rdf > 8192) return fail(PS_ERR_UNSUPPORTED, "ps_batch_create: pairs x thresholds x bins > 8192");
   ps_batch* b = new (std::nothrow) ps_batch();
   if (!b) return fail(PS_ERR_OOM, "host allocation failed");
   b->sw = s;
@@ -597,7 +575,7 @@ int ps_batch_run(ps_batch* b, uint64_t* d_out, void* stream) {
   for (uint32_t q = 0; q < s.n_dsrf; ++q) a.cls_min[q] = s.dsrf_min[q];
   a.acc = b->d_acc;
   a.acc_len = b->acc_len;
-  const uint32_t smem = ((s.bins.n_bins + 1) * 4 + 15) / 16 * 16 + (s.n_pairs * s.n_dsrf * (s.bins.n_bins + 2)) * 4;
+  const uint32_t smem = ((s.bins.n_bins + 1) * 4 + 15) / 16 * 16 + s.n_pairs * s.n_dsrf * ((s.bins.n_bins + 1) * 8 + 4);
   const int sms = b->grids[0]->num_sms;
   int rc;
   const uint32_t k = s.k_max;

@@ -97,8 +97,9 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k,
   uint32_t o = 0;
   L.off_E = o;
   o += (n_bins + 1) * 4;
+  o = (o + 7u) & ~7u;
   L.off_rdf = o;
-  o += rdf ? n_bins * 4 : 0;
+  o += rdf ? n_bins * 8 : 0;
   L.off_knn = o;
   o += n_k * n_bins * 4;
   L.off_kmeta = o;
@@ -114,8 +115,8 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k,
 template <bool RDF>
 struct Hist {
   float* sE;
-  uint32_t* s_rdf;
-  uint32_t* s_knn;
+  unsigned long long* s_rdf;  // 64-bit: per-CTA pair counts can pass 2^32 on large clouds
+  uint32_t* s_knn;            // per-CTA central counts stay below n < 2^32
   uint32_t* s_kmeta;
   float Emax, E0, r0f, inv_dr;
   uint32_t nb;
@@ -123,7 +124,7 @@ struct Hist {
   __device__ void init(const QueryArgs& a, unsigned char* smem, uint32_t stage_cap) {
     const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap);
     sE = reinterpret_cast<float*>(smem + L.off_E);
-    s_rdf = reinterpret_cast<uint32_t*>(smem + L.off_rdf);
+    s_rdf = reinterpret_cast<unsigned long long*>(smem + L.off_rdf);
     s_knn = reinterpret_cast<uint32_t*>(smem + L.off_knn);
     s_kmeta = reinterpret_cast<uint32_t*>(smem + L.off_kmeta);
     nb = a.n_bins;
@@ -133,7 +134,7 @@ struct Hist {
       sE[b] = __double2float_rn(__dmul_rn(e, e));
     }
     if (RDF)
-      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_rdf[b] = 0;
+      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_rdf[b] = 0ull;
     for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x) s_knn[b] = 0;
     for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x) s_kmeta[b] = 0;
     __syncthreads();
@@ -143,15 +144,11 @@ struct Hist {
     inv_dr = (float)(1.0 / a.dr);
   }
 
-  // one in-range pair (d2 < Emax): RDF bin (shared, or global when `glob`)
-  __device__ __forceinline__ void pair(const QueryArgs& a, float d2, bool glob, uint64_t& binned, uint64_t& below) {
+  // one in-range pair (d2 < Emax): RDF bin
+  __device__ __forceinline__ void pair(const QueryArgs& a, float d2, uint64_t& binned, uint64_t& below) {
     if (!RDF) return;
     if (d2 >= E0) {
-      const uint32_t b = bin_index(d2, sE, nb, r0f, inv_dr);
-      if (glob)
-        atomicAdd((unsigned long long*)&a.rdf[b], 1ull);
-      else
-        atomicAdd(&s_rdf[b], 1u);
+      atomicAdd(&s_rdf[bin_index(d2, sE, nb, r0f, inv_dr)], 1ull);
       ++binned;
     } else {
       ++below;
@@ -159,25 +156,16 @@ struct Hist {
   }
 
   // the k-th distance D of one central for the q-th requested k
-  __device__ __forceinline__ void kth(const QueryArgs& a, uint32_t q, float D, uint32_t idx, bool glob) {
+  __device__ __forceinline__ void kth(const QueryArgs& a, uint32_t q, float D, uint32_t idx) {
     if (a.kth) a.kth[(int64_t)q * a.n + idx] = D;
     uint32_t* sp;
-    unsigned long long* gp;
-    if (!(D < Emax)) {
+    if (!(D < Emax))
       sp = &s_kmeta[2 * q];
-      gp = (unsigned long long*)&a.meta[PS_META_HEAD + 2 * q];
-    } else if (D < E0) {
+    else if (D < E0)
       sp = &s_kmeta[2 * q + 1];
-      gp = (unsigned long long*)&a.meta[PS_META_HEAD + 2 * q + 1];
-    } else {
-      const uint32_t b = bin_index(D, sE, nb, r0f, inv_dr);
-      sp = &s_knn[q * nb + b];
-      gp = (unsigned long long*)&a.knn[q * nb + b];
-    }
-    if (glob)
-      atomicAdd(gp, 1ull);
     else
-      atomicAdd(sp, 1u);
+      sp = &s_knn[q * nb + bin_index(D, sE, nb, r0f, inv_dr)];
+    atomicAdd(sp, 1u);
   }
 
   // add the shared counters to the global histograms and clear them (whole CTA)
@@ -185,7 +173,7 @@ struct Hist {
     __syncthreads();
     if (RDF)
       for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
-        if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], (unsigned long long)s_rdf[b]), s_rdf[b] = 0;
+        if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], s_rdf[b]), s_rdf[b] = 0;
     for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x)
       if (s_knn[b]) atomicAdd((unsigned long long*)&a.knn[b], (unsigned long long)s_knn[b]), s_knn[b] = 0;
     for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x)
@@ -232,13 +220,11 @@ __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, IN
 template <int KMAX, bool RDF>
 __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_bound;
   __shared__ float4 s_buf[8][32];
   __shared__ float s_hits[8][32 * 32];  // per warp: the in-range hits of one batch
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   constexpr int KK = KMAX > 0 ? KMAX : 1;
   Hist<RDF> H;
-  if (threadIdx.x == 0) s_bound = 0;
   H.init(a, smem, 0);
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Geo ng = *a.ngeo;
@@ -275,12 +261,6 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     }
     if (lane == 0) rpre[0] = 0;
     __syncwarp();
-    // shared counters take at most 2^31 increments in total; beyond that this warp writes to global
-    unsigned long long old = 0;
-    const unsigned long long inc = (unsigned long long)cnt * ((unsigned long long)n_cand + 1);
-    if (lane == 0) old = atomicAdd(&s_bound, inc);
-    old = __shfl_sync(0xffffffffu, old, 0);
-    const bool glob = old + inc >= (1ull << 31);
 
     // record at virtual candidate position pos (runs concatenated); rr is a run hint, nondecreasing in pos
     auto fetch = [&](uint32_t pos, int& rr) -> float4 {
@@ -345,13 +325,13 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         }
         if (RDF) {
           __syncwarp();
-          for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], glob, my_binned, my_below);
+          for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], my_binned, my_below);
         }
       }
       if (valid) {
         if (a.nwithin) a.nwithin[pidx] = within;
         if (KMAX > 0)
-          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx, glob);
+          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
       }
     } else {
       // few centrals: the lanes split the candidates of each central
@@ -368,7 +348,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
           if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
             ++within;
-            H.pair(a, d2, glob, my_binned, my_below);
+            H.pair(a, d2, my_binned, my_below);
             if (KMAX > 0) topk_insert(top, d2);
           }
         }
@@ -389,7 +369,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
             }
             if (lane == 0)
               for (uint32_t q = 0; q < a.n_k; ++q)
-                if (a.ks[q] == rank + 1) H.kth(a, q, m, pidx, glob);
+                if (a.ks[q] == rank + 1) H.kth(a, q, m, pidx);
           }
         }
       }
@@ -425,7 +405,6 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
   const uint32_t n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   uint32_t phase = 0;
   uint64_t my_binned = 0, my_below = 0;
-  uint64_t bound = 0;  // upper bound of any shared counter since the last flush (uniform)
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(&a.cgeo->work_next, 1u);
@@ -436,16 +415,6 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
     const uint32_t c0 = a.cstart[c], n_c = a.cstart[c + 1] - c0;
     if (tid < n_runs) cell_run(a, ng, c, tid, s_run_src[tid], s_run_len[tid]);
     __syncthreads();
-    uint32_t n_cand = 0;
-    for (uint32_t r = 0; r < n_runs; ++r) n_cand += s_run_len[r];
-
-    // bound the shared 32-bit counters: flush before they could overflow
-    const uint64_t inc = (uint64_t)n_c * ((uint64_t)n_cand + 1);
-    if (bound + inc >= (1ull << 31)) {
-      H.flush(a);
-      bound = 0;
-    }
-    bound += inc;
 
     for (uint32_t cb = 0; cb < n_c; cb += blockDim.x) {
       const uint32_t ci = cb + tid;
@@ -498,7 +467,7 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
               const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
               if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
                 ++within;
-                H.pair(a, d2, false, my_binned, my_below);
+                H.pair(a, d2, my_binned, my_below);
                 if (KMAX > 0) topk_insert(top, d2);
               }
             }
@@ -509,7 +478,7 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
       if (valid) {
         if (a.nwithin) a.nwithin[pidx] = within;
         if (KMAX > 0)
-          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx, false);
+          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
       }
     }
     __syncthreads();  // s_item and the run table are rewritten next

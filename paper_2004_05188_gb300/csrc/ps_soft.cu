@@ -139,10 +139,10 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ uint32_t s_rsrc[8][kSoftRuns], s_rpre[8][kSoftRuns + 1];
-  uint32_t* sM0 = reinterpret_cast<uint32_t*>(smem);
-  float* sM1 = reinterpret_cast<float*>(smem + a.n_fine * 4);
-  float* sM2 = reinterpret_cast<float*>(smem + a.n_fine * 8);
-  for (uint32_t m = threadIdx.x; m < a.n_fine; m += blockDim.x) sM0[m] = 0, sM1[m] = 0.f, sM2[m] = 0.f;
+  unsigned long long* sM0 = reinterpret_cast<unsigned long long*>(smem);  // 64-bit: no per-CTA overflow
+  float* sM1 = reinterpret_cast<float*>(smem + a.n_fine * 8);
+  float* sM2 = reinterpret_cast<float*>(smem + a.n_fine * 12);
+  for (uint32_t m = threadIdx.x; m < a.n_fine; m += blockDim.x) sM0[m] = 0ull, sM1[m] = 0.f, sM2[m] = 0.f;
   __syncthreads();
   const uint32_t w = threadIdx.x >> 5;
   const float s = a.scale, inv_w = a.inv_w, wf = a.w, rc = a.rc;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
     uint32_t m = (uint32_t)(u * inv_w);
     m = m < nf ? m : nf - 1;
     const float delta = u - ((float)m + 0.5f) * wf;
-    atomicAdd(&sM0[m], 1u);
+    atomicAdd(&sM0[m], 1ull);
     atomicAdd(&sM1[m], delta);
     atomicAdd(&sM2[m], delta * delta);
   };
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
   __syncthreads();
   for (uint32_t m = threadIdx.x; m < nf; m += blockDim.x) {
     if (sM0[m]) {
-      atomicAdd(&a.M0[m], (unsigned long long)sM0[m]);
+      atomicAdd(&a.M0[m], sM0[m]);
       atomicAdd(&a.M1[m], (double)sM1[m]);
       atomicAdd(&a.M2[m], (double)sM2[m]);
     }
@@ -386,7 +386,7 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   PS_CUDA(cudaMemsetAsync(g->soft_m0, 0, (size_t)sa.n_fine * 8, s));
   PS_CUDA(cudaMemsetAsync(g->soft_m1, 0, (size_t)sa.n_fine * 8, s));
   PS_CUDA(cudaMemsetAsync(g->soft_m2, 0, (size_t)sa.n_fine * 8, s));
-  const uint32_t smem = sa.n_fine * 12;
+  const uint32_t smem = sa.n_fine * 16;
   int blocks = 0;
   rc = launch_grid_for(g, (const void*)k_soft_fwd, smem, &blocks);
   if (rc) return rc;
