@@ -339,19 +339,27 @@ def measure_batched(args, dev):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, out
 
-    b = ps.Batch(rois, bins, rmax, dsrf, pairs, k_max, args.batch_cell_scale)
+    sub = list(range(0, len(rois), max(1, len(rois) // 16)))[:16]
+    # cell size of the batched kernel: the autotuner's choice on the subset
+    from paper_2004_05188_gb300 import autotune
+
+    cand = (args.batch_cell_scale,) if args.no_autotune else (1.0, 0.5)
+    sub_t = {}
+    for cs in cand:
+        bs = ps.Batch([rois[i] for i in sub], bins, rmax, dsrf, pairs, k_max, cs)
+        sub_t[(cs, 0)] = graph_time(bs)[0]
+        bs.close()
+    best_cs = autotune.choose(sub_t)[0]
+    sub_ms = sub_t[(best_cs, 0)]
+    b = ps.Batch(rois, bins, rmax, dsrf, pairs, k_max, best_cs)
     all_ms, out = graph_time(b)
     meta = out[..., -(4 + 2 * k_max):]
     n_central_all = int(meta[:, 0, -1, 0, 0].sum().item())  # all-all, r_max 3, d_srf >= 0
     b.close()
     del out
 
-    sub = list(range(0, len(rois), max(1, len(rois) // 16)))[:16]
-    bs = ps.Batch([rois[i] for i in sub], bins, rmax, dsrf, pairs, k_max, args.batch_cell_scale)
-    sub_ms, _ = graph_time(bs)
-    bs.close()
     ks = list(range(1, k_max + 1))
-    grids = {i: ps.Grid(rois[i][0].shape[0], args.batch_cell_scale) for i in sub}
+    grids = {i: ps.Grid(rois[i][0].shape[0], best_cs) for i in sub}
 
     def plain_all():
         for i in sub:
@@ -377,10 +385,27 @@ def measure_batched(args, dev):
             "sweep_points": len(rois) * 27, "batched_ms": all_ms,
             "ion_queries_per_s": n_central_all / (all_ms * 1e-3),
             "subset_rois": len(sub), "subset_batched_ms": sub_ms, "subset_plain_ms": plain_ms,
-            "plain_over_batched": plain_ms / sub_ms, "cell_scale": args.batch_cell_scale,
+            "plain_over_batched": plain_ms / sub_ms, "cell_scale": best_cs,
+            "autotune_subset_ms": {f"cell_scale={k[0]}": round(v, 2) for k, v in sub_t.items()},
             "host_generation_s": gen_s,
             "timing": "CUDA events; batched = one CUDA-graph replay (grid builds + one persistent query "
                       "kernel + expansion); plain = one eager ps_spatstat per ROI and sweep point"}
+
+
+def rank_reduce(dist, device, t_max, sums):
+    """Whole-job numbers across ranks: the slowest rank's time and the summed counts.
+
+    dist is torch.distributed (or None for one process); device is where the reduction
+    tensors live (a CUDA device under NCCL, the CPU under gloo)."""
+    import torch
+
+    if dist is None:
+        return float(t_max), [float(x) for x in sums]
+    tt = torch.tensor([float(t_max)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ss = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
+    dist.all_reduce(ss)
+    return float(tt.item()), [float(x) for x in ss.tolist()]
 
 
 def run_gpu(args, wl_name, wl):
@@ -411,7 +436,16 @@ def run_gpu(args, wl_name, wl):
     D = torch.from_numpy(d).to(dev)
     bins = wl["bins"]
     r_cut = float(np.float32(bins[0] + bins[1] * bins[2]))
-    grids = [ps.Grid(N, args.cell_scale, args.dense_min) for _ in wl["combos"]]
+    # kernel configuration per combination: measured by the autotuner on this cloud (untimed)
+    tuned = {}
+    for name, ctr, nbr in wl["combos"]:
+        if args.no_autotune:
+            tuned[name] = {"cell_scale": args.cell_scale, "dense_min": args.dense_min}
+        else:
+            from paper_2004_05188_gb300 import autotune
+
+            tuned[name] = autotune.tune(X, T, D, nbr, ctr, wl["dsrf_min"], wl["bins"], wl["ks"])
+    grids = [ps.Grid(N, tuned[name]["cell_scale"], tuned[name]["dense_min"]) for name, _, _ in wl["combos"]]
     nk = len(wl["ks"])
     outs = []
     for _ in wl["combos"]:
@@ -503,16 +537,7 @@ def run_gpu(args, wl_name, wl):
     launches = ps.launch_count() - lc0 if graph is None else kernels_per_step * args.steps
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    T_ms = float(sum(step_ms))
-    if dist is not None:
-        tt = torch.tensor([T_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        T_ms = float(tt.item())
-        qq = torch.tensor([n_queries, n_pairs], dtype=torch.float64, device=dev)
-        dist.all_reduce(qq)
-        tot_q, tot_p = float(qq[0].item()), float(qq[1].item())
-    else:
-        tot_q, tot_p = float(n_queries), float(n_pairs)
+    T_ms, (tot_q, tot_p) = rank_reduce(dist, dev, float(sum(step_ms)), [n_queries, n_pairs])
     value = tot_q * args.steps / (T_ms * 1e-3)
 
     # ---- e2e through the public API, inputs in pinned host memory ----
@@ -547,11 +572,7 @@ def run_gpu(args, wl_name, wl):
             e2e_step()
             e1[k].record(stream)
         torch.cuda.synchronize()
-        E_ms = float(sum(a.elapsed_time(b) for a, b in zip(e0, e1)))
-        if dist is not None:
-            tt = torch.tensor([E_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            E_ms = float(tt.item())
+        E_ms, _ = rank_reduce(dist, dev, float(sum(a.elapsed_time(b) for a, b in zip(e0, e1))), [])
         h2d = xyz.nbytes + t.nbytes + d.nbytes
         d2h = sum(v.numel() * v.element_size() for o in outs for v in o.values())
         e2e = {"value": tot_q * args.steps / (E_ms * 1e-3), "unit": "ion-queries/s", "h2d_bytes_per_step": h2d,
@@ -597,7 +618,9 @@ def run_gpu(args, wl_name, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "n_ions": N, "centrals_per_step": n_queries,
-                       "cell_scale": args.cell_scale, "dense_min": args.dense_min,
+                       "kernel_config": {k: {"cell_scale": v["cell_scale"], "dense_min": v["dense_min"]}
+                                         for k, v in tuned.items()},
+                       "autotune": {k: v.get("timings_ms") for k, v in tuned.items()},
                        "neighbour_pairs_per_step": n_pairs, "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world} (independent specimens, no collective)"},
             "neighbour_pairs_per_s": tot_p * args.steps / (T_ms * 1e-3),
@@ -628,6 +651,8 @@ def main():
     ap.add_argument("--batch-cell-scale", type=float, default=1.0)
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
+    ap.add_argument("--no-autotune", action="store_true", help="use --cell-scale/--dense-min instead of the autotuner")
+    ap.add_argument("--only-form", choices=["soft", "batched"], help="measure only this form (no exact step line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     wl = dict(WORKLOADS[args.workload])
@@ -638,6 +663,14 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
+    if args.only_form:
+        import torch
+
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        fn = {"soft": measure_soft, "batched": measure_batched}[args.only_form]
+        print(json.dumps({"form": args.only_form, **fn(args, dev)}), flush=True)
+        return 0
     return run_gpu(args, args.workload, wl)
 
 

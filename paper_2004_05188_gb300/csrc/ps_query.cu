@@ -90,16 +90,21 @@ __device__ __forceinline__ uint32_t bin_index(float d2, const float* sE, uint32_
 
 struct SmemLayout {
   uint32_t off_E, off_rdf, off_knn, off_kmeta, off_stage, total;
+  bool priv;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k, bool rdf, uint32_t stage_cap) {
+constexpr uint32_t kPrivBins = 512;  // up to this many bins each warp keeps its own 32-bit RDF row
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k, bool rdf, uint32_t stage_cap,
+                                                  bool allow_priv = false) {
   SmemLayout L;
   uint32_t o = 0;
+  L.priv = allow_priv && rdf && n_bins <= kPrivBins;
   L.off_E = o;
   o += (n_bins + 1) * 4;
   o = (o + 7u) & ~7u;
   L.off_rdf = o;
-  o += rdf ? n_bins * 8 : 0;
+  o += rdf ? (L.priv ? 8 * n_bins * 4 : n_bins * 8) : 0;
   L.off_knn = o;
   o += n_k * n_bins * 4;
   L.off_kmeta = o;
@@ -115,16 +120,20 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k,
 template <bool RDF>
 struct Hist {
   float* sE;
-  unsigned long long* s_rdf;  // 64-bit: per-CTA pair counts can pass 2^32 on large clouds
+  unsigned long long* s_rdf;  // CTA row, 64-bit: per-CTA pair counts can pass 2^32 on large clouds
+  uint32_t* s_rdfw;           // or one 32-bit row per warp (priv), flushed by its warp before it could wrap
+  bool priv;
   uint32_t* s_knn;            // per-CTA central counts stay below n < 2^32
   uint32_t* s_kmeta;
   float Emax, E0, r0f, inv_dr;
   uint32_t nb;
 
-  __device__ void init(const QueryArgs& a, unsigned char* smem, uint32_t stage_cap) {
-    const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap);
+  __device__ void init(const QueryArgs& a, unsigned char* smem, uint32_t stage_cap, bool allow_priv = false) {
+    const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap, allow_priv);
     sE = reinterpret_cast<float*>(smem + L.off_E);
+    priv = L.priv;
     s_rdf = reinterpret_cast<unsigned long long*>(smem + L.off_rdf);
+    s_rdfw = reinterpret_cast<uint32_t*>(smem + L.off_rdf) + (threadIdx.x >> 5) * a.n_bins;
     s_knn = reinterpret_cast<uint32_t*>(smem + L.off_knn);
     s_kmeta = reinterpret_cast<uint32_t*>(smem + L.off_kmeta);
     nb = a.n_bins;
@@ -133,8 +142,12 @@ struct Hist {
       const double e = __dadd_rn(a.r0, __dmul_rn((double)b, a.dr));
       sE[b] = __double2float_rn(__dmul_rn(e, e));
     }
-    if (RDF)
-      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_rdf[b] = 0ull;
+    if (RDF) {
+      if (priv)
+        for (uint32_t b = threadIdx.x; b < 8 * nb; b += blockDim.x) reinterpret_cast<uint32_t*>(s_rdf)[b] = 0;
+      else
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_rdf[b] = 0ull;
+    }
     for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x) s_knn[b] = 0;
     for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x) s_kmeta[b] = 0;
     __syncthreads();
@@ -148,7 +161,11 @@ struct Hist {
   __device__ __forceinline__ void pair(const QueryArgs& a, float d2, uint64_t& binned, uint64_t& below) {
     if (!RDF) return;
     if (d2 >= E0) {
-      atomicAdd(&s_rdf[bin_index(d2, sE, nb, r0f, inv_dr)], 1ull);
+      const uint32_t b = bin_index(d2, sE, nb, r0f, inv_dr);
+      if (priv)
+        atomicAdd(&s_rdfw[b], 1u);
+      else
+        atomicAdd(&s_rdf[b], 1ull);
       ++binned;
     } else {
       ++below;
@@ -168,10 +185,20 @@ struct Hist {
     atomicAdd(sp, 1u);
   }
 
+  // one warp adds its private RDF row to the global histogram and clears it
+  __device__ void flush_warp(const QueryArgs& a) {
+    if (!RDF || !priv) return;
+    __syncwarp();
+    for (uint32_t b = threadIdx.x & 31; b < nb; b += 32)
+      if (s_rdfw[b]) atomicAdd((unsigned long long*)&a.rdf[b], (unsigned long long)s_rdfw[b]), s_rdfw[b] = 0;
+    __syncwarp();
+  }
+
   // add the shared counters to the global histograms and clear them (whole CTA)
   __device__ void flush(const QueryArgs& a) {
+    flush_warp(a);
     __syncthreads();
-    if (RDF)
+    if (RDF && !priv)
       for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
         if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], s_rdf[b]), s_rdf[b] = 0;
     for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x)
@@ -225,8 +252,9 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   constexpr int KK = KMAX > 0 ? KMAX : 1;
   Hist<RDF> H;
-  H.init(a, smem, 0);
+  H.init(a, smem, 0, true);
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
   const Geo ng = *a.ngeo;
   const uint32_t n_items = a.cgeo->work_n2;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
@@ -326,6 +354,11 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         if (RDF) {
           __syncwarp();
           for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], my_binned, my_below);
+          wcount += nh;
+          if (wcount >= (1ull << 31)) {
+            H.flush_warp(a);
+            wcount = 0;
+          }
         }
       }
       if (valid) {
@@ -355,6 +388,11 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) within += __shfl_xor_sync(0xffffffffu, within, o);
         if (lane == 0 && a.nwithin) a.nwithin[pidx] = within;
+        wcount += within;
+        if (wcount >= (1ull << 31)) {
+          H.flush_warp(a);
+          wcount = 0;
+        }
         if (KMAX > 0) {
           // merge the 32 sorted lane lists: pop the warp minimum k_need times
           for (uint32_t rank = 0; rank < a.k_need; ++rank) {
@@ -578,7 +616,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   uint32_t stage_bytes = budget > base.total + 16 * 1024 ? budget - base.total : 16 * 1024;
   qa.stage_cap = (stage_bytes / 16) & ~7u;
   const uint32_t smem_cta = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap).total;
-  const uint32_t smem_warp = base.total;
+  const uint32_t smem_warp = smem_layout(bins.n_bins, n_k, rdf, 0, true).total;
   if (n_k > 0 || rdf) {
     rc = rdf ? dispatch_k<true>(g, qa, smem_cta, smem_warp, s) : dispatch_k<false>(g, qa, smem_cta, smem_warp, s);
     if (rc) return rc;

@@ -72,9 +72,13 @@ __device__ __forceinline__ void soft_run(const SoftArgs& a, const Geo& ng, uint3
 
 // Iterates the items of the owner list; for every owner lane and in-range
 // candidate calls f(lane_has_owner, p (owner record), q (candidate), d2).
-template <class F, class B, class E>
+struct NoHook {
+  __device__ void operator()(uint32_t, uint32_t) const {}
+};
+
+template <class F, class B, class E, class H = NoHook>
 __device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint32_t* rsrc, uint32_t* rpre, F&& f,
-                                           B&& begin_owner, E&& end_owner) {
+                                           B&& begin_owner, E&& end_owner, H&& item_hook = H()) {
   const uint32_t lane = threadIdx.x & 31;
   const Geo ng = *a.ngeo;
   const uint32_t n_items = a.ogeo->work_n2;
@@ -103,6 +107,7 @@ __device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint3
     }
     if (lane == 0) rpre[0] = 0;
     __syncwarp();
+    item_hook(cnt, n_cand);
     const bool valid = lane < cnt;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) p = a.orec[c0 + lane];
@@ -139,11 +144,15 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ uint32_t s_rsrc[8][kSoftRuns], s_rpre[8][kSoftRuns + 1];
-  unsigned long long* sM0 = reinterpret_cast<unsigned long long*>(smem);  // 64-bit: no per-CTA overflow
-  float* sM1 = reinterpret_cast<float*>(smem + a.n_fine * 8);
-  float* sM2 = reinterpret_cast<float*>(smem + a.n_fine * 12);
-  for (uint32_t m = threadIdx.x; m < a.n_fine; m += blockDim.x) sM0[m] = 0ull, sM1[m] = 0.f, sM2[m] = 0.f;
+  // 32-bit counts per CTA; a warp whose item could push the CTA past 2^31 pairs writes to global instead
+  uint32_t* sM0 = reinterpret_cast<uint32_t*>(smem);
+  float* sM1 = reinterpret_cast<float*>(smem + a.n_fine * 4);
+  float* sM2 = reinterpret_cast<float*>(smem + a.n_fine * 8);
+  __shared__ unsigned long long s_pairs;
+  for (uint32_t m = threadIdx.x; m < a.n_fine; m += blockDim.x) sM0[m] = 0, sM1[m] = 0.f, sM2[m] = 0.f;
+  if (threadIdx.x == 0) s_pairs = 0;
   __syncthreads();
+  bool glob = false;
   const uint32_t w = threadIdx.x >> 5;
   const float s = a.scale, inv_w = a.inv_w, wf = a.w, rc = a.rc;
   const uint32_t nf = a.n_fine;
@@ -153,16 +162,29 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
     uint32_t m = (uint32_t)(u * inv_w);
     m = m < nf ? m : nf - 1;
     const float delta = u - ((float)m + 0.5f) * wf;
-    atomicAdd(&sM0[m], 1ull);
-    atomicAdd(&sM1[m], delta);
-    atomicAdd(&sM2[m], delta * delta);
+    if (glob) {
+      atomicAdd(&a.M0[m], 1ull);
+      atomicAdd(&a.M1[m], (double)delta);
+      atomicAdd(&a.M2[m], (double)delta * (double)delta);
+    } else {
+      atomicAdd(&sM0[m], 1u);
+      atomicAdd(&sM1[m], delta);
+      atomicAdd(&sM2[m], delta * delta);
+    }
+  };
+  auto bound = [&](uint32_t cnt, uint32_t n_cand) {
+    unsigned long long old = 0;
+    const unsigned long long inc = (unsigned long long)cnt * n_cand;
+    if ((threadIdx.x & 31) == 0) old = atomicAdd(&s_pairs, inc);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    glob = old + inc >= (1ull << 31);
   };
   auto nop = [](bool, const float4&) {};
-  soft_items(a, s_buf[w], s_rsrc[w], s_rpre[w], pair, nop, nop);
+  soft_items(a, s_buf[w], s_rsrc[w], s_rpre[w], pair, nop, nop, bound);
   __syncthreads();
   for (uint32_t m = threadIdx.x; m < nf; m += blockDim.x) {
     if (sM0[m]) {
-      atomicAdd(&a.M0[m], sM0[m]);
+      atomicAdd(&a.M0[m], (unsigned long long)sM0[m]);
       atomicAdd(&a.M1[m], (double)sM1[m]);
       atomicAdd(&a.M2[m], (double)sM2[m]);
     }
@@ -386,7 +408,7 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   PS_CUDA(cudaMemsetAsync(g->soft_m0, 0, (size_t)sa.n_fine * 8, s));
   PS_CUDA(cudaMemsetAsync(g->soft_m1, 0, (size_t)sa.n_fine * 8, s));
   PS_CUDA(cudaMemsetAsync(g->soft_m2, 0, (size_t)sa.n_fine * 8, s));
-  const uint32_t smem = sa.n_fine * 16;
+  const uint32_t smem = sa.n_fine * 12;
   int blocks = 0;
   rc = launch_grid_for(g, (const void*)k_soft_fwd, smem, &blocks);
   if (rc) return rc;

@@ -1,0 +1,38 @@
+"""Host logic of the autotuner (no GPU): signature, choice, caching."""
+import json
+
+from paper_2004_05188_gb300 import autotune
+
+
+def test_signature_rounds_sizes():
+    a = autotune.signature(8_087_565, 115_871, 100_000, (0.0, 0.01, 200), [1, 5, 10])
+    b = autotune.signature(8_200_000, 118_000, 101_000, (0.0, 0.01, 200), [10, 1])
+    assert a == b
+    assert autotune.signature(200_000, 200_000, 141_169, (0.0, 0.01, 200), [1]) != a
+
+
+def test_choose_fastest_and_ties():
+    assert autotune.choose({(1.0, 0): 2.0, (0.5, 0): 1.5, (1.0, 128): 3.0}) == (0.5, 0)
+    assert autotune.choose({(1.0, 0): 1.0, (0.5, 0): 1.0}) == (1.0, 0)
+
+
+def test_tune_uses_runner_and_caches(tmp_path):
+    calls = []
+
+    def runner(cs, dm):
+        calls.append((cs, dm))
+        return {(1.0, 0): 3.0, (0.75, 0): 2.5, (0.5, 0): 1.0, (1.0, 128): 4.0}[(cs, dm)]
+
+    path = str(tmp_path / "tune.json")
+    r = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1",
+                      cache_path=path)
+    assert (r["cell_scale"], r["dense_min"], r["cached"]) == (0.5, 0, False)
+    assert len(calls) == 4
+    r2 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1")
+    assert r2["cached"] and len(calls) == 4
+    with open(path) as f:
+        assert json.load(f)["k1"]["cell_scale"] == 0.5
+    autotune._cache.clear()
+    r3 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1",
+                       cache_path=path)
+    assert r3["cached"] and len(calls) == 4
