@@ -106,7 +106,8 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   const size_t o_witem = take((size_t)g->item_cap * 8), o_nwitem = take((size_t)g->item_cap * 8);
   const size_t o_sm0 = take(kSoftFineMax * 8), o_sm1 = take(kSoftFineMax * 8), o_sm2 = take(kSoftFineMax * 8);
   const size_t o_sT = take(3 * kSoftFineMax * 4), o_sgs = take(8);
-  const size_t o_part = take((size_t)g->scan_tiles_cap * 4), o_ngeo = take(sizeof(Geo)), o_cgeo = take(sizeof(Geo));
+  const size_t o_part = take((size_t)g->scan_tiles_cap * 8), o_sctr = take(8);
+  const size_t o_ngeo = take(sizeof(Geo)), o_cgeo = take(sizeof(Geo));
   void* base = nullptr;
   e = cudaMalloc(&base, off);
   if (e != cudaSuccess) {
@@ -133,8 +134,11 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   g->soft_T = reinterpret_cast<float*>(b + o_sT);
   g->soft_gs = reinterpret_cast<double*>(b + o_sgs);
   g->ctr.geo = reinterpret_cast<Geo*>(b + o_cgeo);
-  g->scan_part = reinterpret_cast<uint32_t*>(b + o_part);
+  g->scan_state = reinterpret_cast<unsigned long long*>(b + o_part);
+  g->scan_ctr = reinterpret_cast<uint32_t*>(b + o_sctr);
   e = cudaMemset(g->nbr.geo, 0, sizeof(Geo));
+  if (e == cudaSuccess) e = cudaMemset(g->scan_state, 0, (size_t)g->scan_tiles_cap * 8);
+  if (e == cudaSuccess) e = cudaMemset(g->scan_ctr, 0, 8);
   if (e == cudaSuccess) e = cudaMemset(g->ctr.geo, 0, sizeof(Geo));
   if (e != cudaSuccess) {
     cudaFree(base);

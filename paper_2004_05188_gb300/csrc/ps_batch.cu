@@ -40,6 +40,7 @@ struct BRoi {
   const uint2* witem;
   const Geo* cgeo;
   const float* dsrf;
+  uint32_t cap;  // capacity of witem
 };
 
 struct BatchArgs {
@@ -172,11 +173,11 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
     }
     const BRoi R = a.roi[roi];
     const uint32_t l_item = chunk + w - a.item_off[roi];
-    const uint32_t n_items = R.cgeo->work_n2;
+    const uint32_t n_front = R.cgeo->work_n2, n_items = n_front + R.cgeo->work_n3;
     unsigned long long* A = a.acc + (size_t)roi * a.acc_len;
     if (l_item < n_items) {
       const Geo ng = *R.ngeo;
-      const uint2 it = R.witem[l_item];
+      const uint2 it = work_item(R.witem, R.cap, n_front, l_item);
       const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
       const uint32_t c0 = R.cstart[c] + first;
       // run table
@@ -328,7 +329,7 @@ __global__ void k_batch_offsets(const BRoi* __restrict__ roi, uint32_t n_roi, ui
     uint32_t acc = 0;
     for (uint32_t r = 0; r < n_roi; ++r) {
       item_off[r] = acc;
-      const uint32_t n = roi[r].cgeo->work_n2;
+      const uint32_t n = roi[r].cgeo->work_n2 + roi[r].cgeo->work_n3;
       acc += (n + kChunk - 1) / kChunk * kChunk;
     }
     item_off[n_roi] = acc;
@@ -509,7 +510,8 @@ int ps_batch_create(const ps_dataset* ds, int n_ds, const ps_sweep* sw, ps_batch
   std::vector<BRoi> h(n_ds);
   for (int i = 0; i < n_ds; ++i) {
     ps_grid* g = b->grids[i];
-    h[i] = BRoi{g->nbr.rec, g->nbr.start, g->nbr.geo, g->ctr.rec, g->ctr.start, g->ctr.witem, g->ctr.geo, ds[i].dsrf};
+    h[i] = BRoi{g->nbr.rec, g->nbr.start, g->nbr.geo, g->ctr.rec,       g->ctr.start,
+                g->ctr.witem, g->ctr.geo,  ds[i].dsrf, g->item_cap};
   }
   e = cudaMemcpy(b->d_roi, h.data(), sizeof(BRoi) * n_ds, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_rbins, s.rmax_bins, sizeof(uint32_t) * 4, cudaMemcpyHostToDevice);

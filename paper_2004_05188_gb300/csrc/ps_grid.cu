@@ -77,7 +77,7 @@ __global__ void k_reset(Geo* geo) {
     }
     geo->n_sel = 0;
     geo->status = 0;
-    geo->work_n = geo->work_n2 = 0;
+    geo->work_n = geo->work_n2 = geo->work_n3 = 0;
     geo->work_next = geo->work_next2 = 0;
   }
 }
@@ -300,7 +300,7 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     *cgeo = *ngeo;
     cgeo->n_sel = 0;
     cgeo->status = 0;
-    cgeo->work_n = cgeo->work_n2 = 0;
+    cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = 0;
     cgeo->work_next = cgeo->work_next2 = 0;
   }
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) count[c] = 0;
@@ -334,55 +334,45 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return prefix + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ count,
-                                                             const Geo* __restrict__ geo, uint32_t* __restrict__ part) {
-  __shared__ uint32_t s_warp[32];
-  const uint32_t nc = geo->n_cells;
-  const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
-  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const uint32_t c0 = t * kScanTile + threadIdx.x * kScanItems;
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) sum += (c0 + k < nc) ? count[c0 + k] : 0u;
-    uint32_t total;
-    block_exclusive_scan(sum, s_warp, total);
-    if (threadIdx.x == 0) part[t] = total;
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_parts(uint32_t* __restrict__ part, const Geo* __restrict__ geo,
-                                                             uint32_t* __restrict__ start) {
-  __shared__ uint32_t s_warp[32];
-  const uint32_t nc = geo->n_cells;
-  const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
-  uint32_t carry = 0;
-  for (uint32_t b = 0; b < tiles; b += blockDim.x) {
-    const uint32_t t = b + threadIdx.x;
-    const uint32_t v = t < tiles ? part[t] : 0u;
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan(v, s_warp, total);
-    if (t < tiles) part[t] = carry + ex;
-    carry += total;
-  }
-  if (threadIdx.x == 0) start[nc] = carry;  // end sentinel: number of records
-}
-
 // Warp items of a cell with n centrals: n <= 3 gives one item (the lanes of
 // the warp split the candidates of each central); otherwise ceil(n/32)
 // balanced batches of at most 32 centrals (one lane per central).
 __device__ __forceinline__ uint32_t items_of(uint32_t n) { return n == 0 ? 0u : (n <= 3 ? 1u : (n + 31u) / 32u); }
 
-// Writes start[] and, for the central list, the work lists: cells with at
-// least dense_min centrals go to `work` (CTA kernel), the others are split
-// into warp items (cell, first << 6 | count) in `witem`.
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ count,
-                                                             const uint32_t* __restrict__ part, Geo* geo,
-                                                             uint32_t* __restrict__ start, uint32_t* __restrict__ work,
-                                                             uint2* __restrict__ witem, uint32_t dense_min) {
+// look-back words: flag in bits 62-63 (1: tile aggregate, 2: inclusive prefix), value in bits 0-31
+constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Single-pass exclusive scan of the cell counts (decoupled look-back).  Tiles
+// are numbered in the order CTAs claim them, so every tile a CTA looks back at
+// belongs to a CTA that is already running or done; the wait on a predecessor
+// is bounded (reports PS_ERR_TIMEOUT) and the last CTA to finish clears the
+// look-back words for the next scan.  Also writes the end sentinel and, for the
+// central list, the work lists: cells with at least dense_min centrals go to
+// `work` (CTA kernel), the others are split into warp items (cell,
+// first << 6 | count), cells with at least kHeavy centrals from the front of
+// `witem`, the rest from the back.
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ count, Geo* geo,
+                                                       uint32_t* __restrict__ start, uint32_t* __restrict__ work,
+                                                       uint2* __restrict__ witem, uint32_t dense_min, uint32_t cap,
+                                                       unsigned long long* state, uint32_t* ctr) {
   __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_tile, s_prefix;
   const uint32_t nc = geo->n_cells;
   const uint32_t tiles = (nc + kScanTile - 1) / kScanTile;
-  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[0], 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= tiles) break;
     const uint32_t c0 = t * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems], sum = 0;
 #pragma unroll
@@ -391,22 +381,51 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
       sum += v[k];
     }
     uint32_t total;
-    uint32_t run = part[t] + block_exclusive_scan(sum, s_warp, total);
+    const uint32_t excl = block_exclusive_scan(sum, s_warp, total);
+    if (threadIdx.x == 0) {
+      uint32_t prefix = 0;
+      if (t > 0) {
+        st_release(&state[t], kFlagA | total);
+        int j = (int)t - 1;
+        uint64_t t0 = 0;
+        while (j >= 0) {
+          const unsigned long long w = ld_acquire(&state[j]);
+          if ((w >> 62) == 0) {
+            if (t0 == 0) t0 = global_ns();
+            if (global_ns() - t0 > kWaitLimitNs) {
+              atomicCAS(&geo->status, 0, (int)PS_ERR_TIMEOUT);
+              break;
+            }
+            continue;
+          }
+          prefix += (uint32_t)w;
+          if ((w >> 62) == 2) break;
+          --j;
+          t0 = 0;
+        }
+      }
+      st_release(&state[t], kFlagP | (uint32_t)(prefix + total));
+      s_prefix = prefix;
+      if (t == tiles - 1) start[nc] = prefix + total;  // end sentinel: number of records
+    }
+    __syncthreads();
+    uint32_t run = s_prefix + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       if (c0 + k < nc) start[c0 + k] = run;
       run += v[k];
     }
     if (work != nullptr) {
-      uint32_t n_items = 0;
+      uint32_t n_heavy = 0, n_light = 0;
 #pragma unroll
       for (int k = 0; k < kScanItems; ++k) {
         const bool dense = (c0 + k < nc) && v[k] >= dense_min;
         const uint32_t s1 = warp_append(dense, &geo->work_n);
         if (dense) work[s1] = c0 + k;
-        if (!dense) n_items += items_of(v[k]);
+        if (!dense) (v[k] >= kHeavy ? n_heavy : n_light) += items_of(v[k]);
       }
-      uint32_t slot = warp_append_n(n_items, &geo->work_n2);
+      uint32_t hs = warp_append_n(n_heavy, &geo->work_n2);
+      uint32_t ls = warp_append_n(n_light, &geo->work_n3);
 #pragma unroll
       for (int k = 0; k < kScanItems; ++k) {
         if (v[k] >= dense_min) continue;
@@ -416,10 +435,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
         uint32_t first = 0;
         for (uint32_t q = 0; q < m; ++q) {
           const uint32_t cnt = base + (q < rem ? 1u : 0u);
-          witem[slot++] = make_uint2(c0 + k, (first << 6) | cnt);
+          const uint2 it = make_uint2(c0 + k, (first << 6) | cnt);
+          if (v[k] >= kHeavy)
+            witem[hs++] = it;
+          else
+            witem[cap - 1 - ls++] = it;
           first += cnt;
         }
       }
+    }
+    __syncthreads();  // s_tile and s_prefix are rewritten next
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {
+      for (uint32_t i = 0; i < tiles; ++i) state[i] = 0ull;
+      ctr[0] = 0;
+      __threadfence();
+      ctr[1] = 0;
     }
   }
 }
@@ -445,12 +478,10 @@ static int grid_blocks(const ps_grid* g, int per_sm) { return g->num_sms * per_s
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStream_t s) {
-  const int nb = grid_blocks(g, 1);
-  PS_LAUNCH(PS_KID_SCAN, s, k_scan_tiles<<<nb, kScanThreads, 0, s>>>(L.count, geo, g->scan_part));
-  PS_LAUNCH(PS_KID_SCAN, s, k_scan_parts<<<1, kScanThreads, 0, s>>>(g->scan_part, geo, L.start));
   PS_LAUNCH(PS_KID_SCAN, s,
-            k_scan_apply<<<nb, kScanThreads, 0, s>>>(L.count, g->scan_part, geo, L.start,
-                                                     with_work ? L.work : nullptr, L.witem, g->dense_min));
+            k_scan<<<grid_blocks(g, 1), kScanThreads, 0, s>>>(L.count, geo, L.start, with_work ? L.work : nullptr,
+                                                               L.witem, g->dense_min, g->item_cap, g->scan_state,
+                                                               g->scan_ctr));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

@@ -51,7 +51,16 @@ struct Geo {
   uint32_t work_n2;    // warp items in witem[] (warp kernel)
   uint32_t work_next;  // persistent-kernel work counters
   uint32_t work_next2;
+  uint32_t work_n3;    // light warp items (cells with < kHeavy centrals), witem[cap-1] downwards
 };
+
+// Warp items with at least this many centrals per cell are listed first (largest work first).
+constexpr uint32_t kHeavy = 16;
+
+// item i of a list whose heavy items grow from the front and light items from the back
+__device__ __forceinline__ uint2 work_item(const uint2* witem, uint32_t cap, uint32_t n_front, uint32_t i) {
+  return i < n_front ? witem[i] : witem[cap - 1 - (i - n_front)];
+}
 
 // A sorted cell list: count / start per cell and the sorted records.
 struct CellList {
@@ -85,7 +94,8 @@ struct ps_grid {
   bool pack_type = false;      // records carry (index << 8 | type) instead of the index (batched sweeps)
   uint32_t* sel = nullptr;     // [n_max] selected ion indices
   uint2* cr = nullptr;         // [n_max] (cell, rank) of selected ions
-  uint32_t* scan_part = nullptr;  // [scan tiles]
+  unsigned long long* scan_state = nullptr;  // [scan tiles] look-back words of the single-pass scan
+  uint32_t* scan_ctr = nullptr;              // [2] tile counter, finished-block counter
   uint32_t scan_tiles_cap = 0;
   // smoothed RDF scratch (fine grid of at most kSoftFineMax bins)
   unsigned long long* soft_m0 = nullptr;

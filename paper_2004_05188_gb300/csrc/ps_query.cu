@@ -40,6 +40,7 @@ struct QueryArgs {
   const uint32_t* cstart;
   const uint32_t* cwork;
   const uint2* witem;
+  uint32_t work_cap;  // capacity of witem (light items grow from its end)
   Geo* cgeo;
   int stencil;
   double r0, dr;
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
   const Geo ng = *a.ngeo;
-  const uint32_t n_items = a.cgeo->work_n2;
+  const uint32_t n_front = a.cgeo->work_n2, n_items = n_front + a.cgeo->work_n3;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   uint64_t my_binned = 0, my_below = 0;
   float4* buf = s_buf[w];
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     if (lane == 0) item = atomicAdd(&a.cgeo->work_next2, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) break;
-    const uint2 it = a.witem[item];
+    const uint2 it = work_item(a.witem, a.work_cap, n_front, item);
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.cstart[c] + first;
     // run table: sources and prefix counts of the candidate runs
@@ -580,6 +581,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.cstart = g->ctr.start;
   qa.cwork = g->ctr.work;
   qa.witem = g->ctr.witem;
+  qa.work_cap = g->item_cap;
   qa.cgeo = g->ctr.geo;
   qa.stencil = g->stencil;
   qa.r0 = bins.r0;

@@ -33,7 +33,8 @@ struct SoftArgs {
   const float4* orec;
   const uint32_t* ostart;
   const uint2* oitem;
-  Geo* ogeo;        // owner list counters (work_n2 items, work_next2)
+  uint32_t ocap;    // capacity of oitem
+  Geo* ogeo;        // owner list counters (work_n2 + work_n3 items, work_next2)
   // candidates and their cell starts (same geometry as the owners)
   const float4* nrec;
   const uint32_t* nstart;
@@ -81,14 +82,14 @@ __device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint3
                                            B&& begin_owner, E&& end_owner, H&& item_hook = H()) {
   const uint32_t lane = threadIdx.x & 31;
   const Geo ng = *a.ngeo;
-  const uint32_t n_items = a.ogeo->work_n2;
+  const uint32_t n_front = a.ogeo->work_n2, n_items = n_front + a.ogeo->work_n3;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(&a.ogeo->work_next2, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_items) break;
-    const uint2 it = a.oitem[item];
+    const uint2 it = work_item(a.oitem, a.ocap, n_front, item);
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.ostart[c] + first;
     uint32_t src = 0, len = 0;
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(256) k_make_items(const uint32_t* __restrict__
 }
 
 __global__ void k_reset_items(Geo* geo) {
-  if (threadIdx.x == 0) geo->work_n2 = 0, geo->work_next2 = 0;
+  if (threadIdx.x == 0) geo->work_n2 = 0, geo->work_n3 = 0, geo->work_next2 = 0;
 }
 
 __global__ void k_reset_counter(Geo* geo) {
@@ -398,6 +399,7 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   sa.orec = g->ctr.rec;
   sa.ostart = g->ctr.start;
   sa.oitem = g->ctr.witem;
+  sa.ocap = g->item_cap;
   sa.ogeo = g->ctr.geo;
   sa.nrec = g->nbr.rec;
   sa.nstart = g->nbr.start;
@@ -445,6 +447,7 @@ int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
   sa.orec = g->ctr.rec;
   sa.ostart = g->ctr.start;
   sa.oitem = g->ctr.witem;
+  sa.ocap = g->item_cap;
   sa.ogeo = g->ctr.geo;
   sa.nrec = g->nbr.rec;
   sa.nstart = g->nbr.start;
@@ -457,6 +460,7 @@ int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
   sa.orec = g->nbr.rec;
   sa.ostart = g->nbr.start;
   sa.oitem = g->nbr_witem;
+  sa.ocap = g->item_cap;
   sa.ogeo = g->nbr.geo;
   sa.nrec = g->ctr.rec;
   sa.nstart = g->ctr.start;

@@ -41,7 +41,8 @@ constexpr size_t o_crec = o_cstart + align256((kCells + 1) * 4);
 constexpr size_t o_cwork = o_crec + align256(kN * 16);
 constexpr size_t o_witem = o_cwork + align256(kCells * 4);
 constexpr size_t o_part = o_witem + align256(kItems * 8);
-constexpr size_t o_ngeo = o_part + align256(kTiles * 4);
+constexpr size_t o_sctr = o_part + align256(kTiles * 8);
+constexpr size_t o_ngeo = o_sctr + align256(8);
 constexpr size_t o_cgeo = o_ngeo + align256(sizeof(Geo));
 constexpr size_t kBytes = o_cgeo + align256(sizeof(Geo));
 
@@ -108,7 +109,8 @@ extern "C" int ps_spatstat_static(const float* xyz, const uint8_t* type, const f
   g.ctr.work = reinterpret_cast<uint32_t*>(b + o_cwork);
   g.ctr.witem = reinterpret_cast<uint2*>(b + o_witem);
   g.ctr.geo = reinterpret_cast<Geo*>(b + o_cgeo);
-  g.scan_part = reinterpret_cast<uint32_t*>(b + o_part);
+  g.scan_state = reinterpret_cast<unsigned long long*>(b + o_part);  // zero at load; each scan clears it again
+  g.scan_ctr = reinterpret_cast<uint32_t*>(b + o_sctr);
   // The build kernels clear every counter and geometry field before use, so the
   // previous call's contents never leak into this one.
   int rc = ps_grid_build(&g, xyz, type, n, nbr_mask, r_cut, stream);
