@@ -99,6 +99,8 @@ __device__ __forceinline__ uint32_t bbin(float d2, const float* sE, uint32_t nb,
 
 template <int KMAX, int NL>
 __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
+  griddep_wait();
+  griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ float s_hd[8][512];
@@ -325,6 +327,8 @@ __global__ void __launch_bounds__(256, 3) k_batch_query(const BatchArgs a) {
 // Padded item offsets: item_off[r] = sum over ROIs before r of ceil(items / kChunk) * kChunk.
 __global__ void k_batch_offsets(const BRoi* __restrict__ roi, uint32_t n_roi, uint32_t* __restrict__ item_off,
                                 uint32_t* __restrict__ next) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) {
     uint32_t acc = 0;
     for (uint32_t r = 0; r < n_roi; ++r) {
@@ -342,6 +346,8 @@ __global__ void k_batch_offsets(const BRoi* __restrict__ roi, uint32_t n_roi, ui
 __global__ void __launch_bounds__(256) k_batch_expand(const unsigned long long* __restrict__ acc, uint32_t acc_len,
                                                       uint32_t nb, uint32_t P, uint32_t C, uint32_t kmax, uint32_t R,
                                                       const uint32_t* __restrict__ rbins, unsigned long long* out) {
+  griddep_wait();
+  griddep_launch();
   const uint32_t rec = nb + kmax * nb + PS_META_LEN(kmax);
   const uint32_t blk = acc_block(nb, kmax);
   const uint32_t id = blockIdx.x;  // ((roi * P + p) * R + r) * C + q
@@ -419,7 +425,7 @@ static int launch_batch(const ps_batch* b, const BatchArgs& a, uint32_t smem, in
   int per_sm = 0;
   PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
   if (per_sm < 1) return fail(PS_ERR_UNSUPPORTED, "batched query kernel does not fit on an SM");
-  PS_LAUNCH(PS_KID_BATCH, st, kern<<<sms * per_sm, 256, smem, st>>>(a));
+  PS_LAUNCH(PS_KID_BATCH, st, PS_CUDA(launch_pdl(kern, sms * per_sm, 256, smem, st, a)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -553,7 +559,7 @@ int ps_batch_run(ps_batch* b, uint64_t* d_out, void* stream) {
     if (rc) return rc;
   }
   PS_CUDA(cudaMemsetAsync(b->d_acc, 0, sizeof(unsigned long long) * (size_t)b->acc_len * n_roi, st));
-  PS_LAUNCH(PS_KID_BATCH, st, k_batch_offsets<<<1, 32, 0, st>>>(b->d_roi, n_roi, b->d_item_off, b->d_next));
+  PS_LAUNCH(PS_KID_BATCH, st, PS_CUDA(launch_pdl(k_batch_offsets, 1, 32, 0, st, b->d_roi, n_roi, b->d_item_off, b->d_next)));
   BatchArgs a;
   memset(&a, 0, sizeof(a));
   a.roi = b->d_roi;
@@ -594,8 +600,8 @@ int ps_batch_run(ps_batch* b, uint64_t* d_out, void* stream) {
   if (rc) return rc;
   const uint32_t n_out = n_roi * s.n_pairs * s.n_rmax * s.n_dsrf;
   PS_LAUNCH(PS_KID_BATCH, st,
-            k_batch_expand<<<n_out, 256, 0, st>>>(b->d_acc, b->acc_len, s.bins.n_bins, s.n_pairs, s.n_dsrf, s.k_max,
-                                                  s.n_rmax, b->d_rbins, reinterpret_cast<unsigned long long*>(d_out)));
+            PS_CUDA(launch_pdl(k_batch_expand, n_out, 256, 0, st, b->d_acc, b->acc_len, s.bins.n_bins, s.n_pairs, s.n_dsrf, s.k_max,
+                                                  s.n_rmax, b->d_rbins, reinterpret_cast<unsigned long long*>(d_out))));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

@@ -70,6 +70,8 @@ __device__ __forceinline__ void load_types16(const uint8_t* __restrict__ type, i
 }
 
 __global__ void k_reset(Geo* geo) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
       geo->bbox_key[a] = f2key(INFINITY);
@@ -96,6 +98,8 @@ __device__ __forceinline__ void box_add(float (&lo)[3], float (&hi)[3], bool& ba
 __global__ void __launch_bounds__(kThreads) k_select_bbox(const float* __restrict__ xyz, const uint8_t* __restrict__ type,
                                                           int64_t n, Mask mask, bool vec, uint32_t* __restrict__ sel,
                                                           Geo* geo) {
+  griddep_wait();
+  griddep_launch();
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
   const int64_t groups = (n + kGroup - 1) / kGroup;
@@ -204,6 +208,8 @@ __device__ void compute_geometry(const Geo& in, float r_cut, float cell_scale, u
 // One thread per block computes the geometry; block 0 publishes it; all zero the counts.
 __global__ void __launch_bounds__(kThreads) k_geometry_zero(Geo* geo, float r_cut, float cell_scale, uint32_t cell_cap,
                                                             uint32_t* __restrict__ count) {
+  griddep_wait();
+  griddep_launch();
   __shared__ uint32_t s_nc;
   if (threadIdx.x == 0) {
     Geo g = *geo;
@@ -225,6 +231,8 @@ __global__ void __launch_bounds__(kThreads) k_geometry_zero(Geo* geo, float r_cu
 __global__ void __launch_bounds__(kThreads) k_count(const float* __restrict__ xyz, const uint32_t* __restrict__ sel,
                                                     const Geo* __restrict__ geo, uint32_t* __restrict__ count,
                                                     uint2* __restrict__ cr) {
+  griddep_wait();
+  griddep_launch();
   const Geo g = *geo;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < g.n_sel; s += gridDim.x * blockDim.x) {
     const uint32_t i = sel[s];
@@ -240,6 +248,8 @@ __global__ void __launch_bounds__(kThreads) k_central_select_count(const float* 
                                                                    float dsrf_min, bool vec, const Geo* __restrict__ ngeo,
                                                                    Geo* cgeo, uint32_t* __restrict__ count,
                                                                    uint32_t* __restrict__ sel, uint2* __restrict__ cr) {
+  griddep_wait();
+  griddep_launch();
   const Geo g = *ngeo;
   bool bad = false;
   const int64_t groups = (n + kGroup - 1) / kGroup;
@@ -294,7 +304,11 @@ __global__ void __launch_bounds__(kThreads) k_central_select_count(const float* 
   if (bad) atomicCAS(&cgeo->status, 0, (int)PS_ERR_INVALID_INPUT);
 }
 
-__global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_t* __restrict__ count) {
+// Resets the central list (copies the neighbour geometry, zeroes the counters
+// and cell counts) and zeroes the query's output arrays.
+__global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_t* __restrict__ count, ZeroOut z) {
+  griddep_wait();
+  griddep_launch();
   const uint32_t nc = ngeo->n_cells;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *cgeo = *ngeo;
@@ -303,7 +317,11 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = 0;
     cgeo->work_next = cgeo->work_next2 = 0;
   }
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) count[c] = 0;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (uint32_t c = tid; c < nc; c += stride) count[c] = 0;
+  for (int k = 0; k < 3; ++k)
+    if (z.p[k])
+      for (uint32_t i = tid; i < z.n[k]; i += stride) z.p[k][i] = 0ull;
 }
 
 // ---- exclusive scan of the cell counts ------------------------------------
@@ -364,6 +382,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
                                                        uint32_t* __restrict__ start, uint32_t* __restrict__ work,
                                                        uint2* __restrict__ witem, uint32_t dense_min, uint32_t cap,
                                                        unsigned long long* state, uint32_t* ctr) {
+  griddep_wait();
+  griddep_launch();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_tile, s_prefix;
   const uint32_t nc = geo->n_cells;
@@ -463,6 +483,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const float* __restrict__ 
                                                       const uint2* __restrict__ cr, const uint32_t* __restrict__ start,
                                                       const Geo* __restrict__ cnt, float4* __restrict__ rec,
                                                       const uint8_t* __restrict__ type) {
+  griddep_wait();
+  griddep_launch();
   const uint32_t ns = cnt->n_sel;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
     const uint32_t i = sel[s];
@@ -479,9 +501,9 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStream_t s) {
   PS_LAUNCH(PS_KID_SCAN, s,
-            k_scan<<<grid_blocks(g, 1), kScanThreads, 0, s>>>(L.count, geo, L.start, with_work ? L.work : nullptr,
+            PS_CUDA(launch_pdl(k_scan, grid_blocks(g, 1), kScanThreads, 0, s, L.count, geo, L.start, with_work ? L.work : nullptr,
                                                                L.witem, g->dense_min, g->item_cap, g->scan_state,
-                                                               g->scan_ctr));
+                                                               g->scan_ctr)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -491,38 +513,39 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
   for (int w = 0; w < 4; ++w) m.w[w] = nbr_mask[w];
   Geo* geo = g->nbr.geo;
   const bool vec = aligned16(g->type) && aligned16(g->xyz);
-  PS_LAUNCH(PS_KID_RESET, s, k_reset<<<1, 32, 0, s>>>(geo));
+  PS_LAUNCH(PS_KID_RESET, s, PS_CUDA(launch_pdl(k_reset, 1, 32, 0, s, geo)));
   if (g->n > 0)
     PS_LAUNCH(PS_KID_SELECT, s,
-              k_select_bbox<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, g->n, m, vec, g->sel, geo));
+              PS_CUDA(launch_pdl(k_select_bbox, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->type, g->n, m, vec, g->sel, geo)));
   PS_LAUNCH(PS_KID_GEOMETRY, s,
-            k_geometry_zero<<<grid_blocks(g, 4), kThreads, 0, s>>>(geo, r_cut, g->cell_scale, g->cell_cap, g->nbr.count));
-  PS_LAUNCH(PS_KID_COUNT, s, k_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, geo, g->nbr.count, g->cr));
+            PS_CUDA(launch_pdl(k_geometry_zero, grid_blocks(g, 4), kThreads, 0, s, geo, r_cut, g->cell_scale, g->cell_cap, g->nbr.count)));
+  PS_LAUNCH(PS_KID_COUNT, s, PS_CUDA(launch_pdl(k_count, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->sel, geo, g->nbr.count, g->cr)));
   int rc = scan_cells(g, g->nbr, geo, false, s);
   if (rc) return rc;
   PS_LAUNCH(PS_KID_SCATTER, s,
-            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec,
-                                                             g->pack_type ? g->type : nullptr));
+            PS_CUDA(launch_pdl(k_scatter, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->sel, g->cr, g->nbr.start, geo, g->nbr.rec,
+                                                             g->pack_type ? g->type : nullptr)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
-int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s) {
+int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
+                       ZeroOut z) {
   Mask m;
   for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w];
   const bool vec = aligned16(g->type) && aligned16(g->xyz) && (dsrf == nullptr || aligned16(dsrf));
   PS_LAUNCH(PS_KID_CENTRAL, s,
-            k_central_reset<<<grid_blocks(g, 4), kThreads, 0, s>>>(g->nbr.geo, g->ctr.geo, g->ctr.count));
+            PS_CUDA(launch_pdl(k_central_reset, grid_blocks(g, 4), kThreads, 0, s, g->nbr.geo, g->ctr.geo, g->ctr.count, z)));
   if (g->n > 0)
     PS_LAUNCH(PS_KID_CENTRAL, s,
-              k_central_select_count<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->type, dsrf, g->n, m, dsrf_min,
+              PS_CUDA(launch_pdl(k_central_select_count, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->type, dsrf, g->n, m, dsrf_min,
                                                                               vec, g->nbr.geo, g->ctr.geo, g->ctr.count,
-                                                                              g->sel, g->cr));
+                                                                              g->sel, g->cr)));
   int rc = scan_cells(g, g->ctr, g->ctr.geo, true, s);
   if (rc) return rc;
   PS_LAUNCH(PS_KID_SCATTER, s,
-            k_scatter<<<grid_blocks(g, 8), kThreads, 0, s>>>(g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec,
-                                                             g->pack_type ? g->type : nullptr));
+            PS_CUDA(launch_pdl(k_scatter, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec,
+                                                             g->pack_type ? g->type : nullptr)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

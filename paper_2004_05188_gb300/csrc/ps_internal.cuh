@@ -29,6 +29,28 @@ void prof_end(uint32_t kid, cudaStream_t s);
     ps::prof_end((kid), (s));   \
   } while (0)
 
+// Programmatic dependent launch: a kernel may be scheduled while its predecessor
+// drains.  Every kernel of the library starts with griddep_wait(), which returns
+// once the predecessor grid has completed and its memory is visible, so the
+// order of effects is the stream order; only the launch latency overlaps.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 #define PS_CUDA(call)                                   \
   do {                                                  \
     cudaError_t e_ = (call);                            \
@@ -134,7 +156,13 @@ __host__ __device__ inline float key2f(int32_t k) {
 
 // host-side builders shared between translation units
 int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cudaStream_t s);
-int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s);
+// output arrays a central-list reset also zeroes (null pointers are skipped)
+struct ZeroOut {
+  uint64_t* p[3] = {nullptr, nullptr, nullptr};
+  uint32_t n[3] = {0, 0, 0};
+};
+int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
+                       ZeroOut z = ZeroOut());
 int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                  ps_bins bins, float* d_h, cudaStream_t s);
 int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,

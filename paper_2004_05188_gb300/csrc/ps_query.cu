@@ -247,6 +247,8 @@ __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, IN
 // ---------------------------------------------------------------------------
 template <int KMAX, bool RDF>
 __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
+  griddep_wait();
+  griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ float s_hits[8][32 * 32];  // per warp: the in-range hits of one batch
@@ -423,6 +425,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
 // ---------------------------------------------------------------------------
 template <int KMAX, bool RDF>
 __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
+  griddep_wait();
+  griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t s_item;
@@ -529,6 +533,8 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
 
 // Writes n_central and the device status into the meta array.
 __global__ void k_query_epilogue(const Geo* __restrict__ ngeo, const Geo* __restrict__ cgeo, uint64_t* meta) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) {
     meta[PS_META_N_CENTRAL] = cgeo->n_sel;
     int st = cgeo->status;
@@ -550,9 +556,9 @@ static int launch_query(const ps_grid* g, const QueryArgs& qa, uint32_t smem_cta
     int per_sm_c = 0;
     PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kc, 256, smem_cta));
     if (per_sm_c < 1) return fail(PS_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
-    PS_LAUNCH(PS_KID_QUERY, s, kc<<<g->num_sms * per_sm_c, 256, smem_cta, s>>>(qa));
+    PS_LAUNCH(PS_KID_QUERY, s, PS_CUDA(launch_pdl(kc, g->num_sms * per_sm_c, 256, smem_cta, s, qa)));
   }
-  PS_LAUNCH(PS_KID_QUERY, s, kw<<<g->num_sms * per_sm_w, 256, smem_warp, s>>>(qa));
+  PS_LAUNCH(PS_KID_QUERY, s, PS_CUDA(launch_pdl(kw, g->num_sms * per_sm_w, 256, smem_warp, s, qa)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -601,11 +607,13 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.n = g->n;
 
   const bool rdf = d_rdf != nullptr;
-  PS_CUDA(cudaMemsetAsync(d_meta, 0, PS_META_LEN(n_k) * sizeof(uint64_t), s));
-  if (rdf) PS_CUDA(cudaMemsetAsync(d_rdf, 0, (size_t)bins.n_bins * sizeof(uint64_t), s));
-  if (n_k) PS_CUDA(cudaMemsetAsync(d_knn, 0, (size_t)n_k * bins.n_bins * sizeof(uint64_t), s));
+  ZeroOut z;  // the outputs are zeroed by the central-list reset kernel
+  z.p[0] = d_meta;
+  z.n[0] = PS_META_LEN(n_k);
+  if (rdf) z.p[1] = d_rdf, z.n[1] = bins.n_bins;
+  if (n_k) z.p[2] = d_knn, z.n[2] = n_k * bins.n_bins;
 
-  int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s);
+  int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z);
   if (rc) return rc;
 
   // staging budget of the CTA kernel: two CTAs per SM
@@ -623,7 +631,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
     rc = rdf ? dispatch_k<true>(g, qa, smem_cta, smem_warp, s) : dispatch_k<false>(g, qa, smem_cta, smem_warp, s);
     if (rc) return rc;
   }
-  PS_LAUNCH(PS_KID_EPILOGUE, s, k_query_epilogue<<<1, 32, 0, s>>>(g->nbr.geo, g->ctr.geo, d_meta));
+  PS_LAUNCH(PS_KID_EPILOGUE, s, PS_CUDA(launch_pdl(k_query_epilogue, 1, 32, 0, s, g->nbr.geo, g->ctr.geo, d_meta)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

@@ -142,6 +142,8 @@ __device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint3
 // forward: fine-grid moments
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
+  griddep_wait();
+  griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ uint32_t s_rsrc[8][kSoftRuns], s_rpre[8][kSoftRuns + 1];
@@ -207,6 +209,8 @@ __global__ void __launch_bounds__(256) k_soft_finalize(const unsigned long long*
                                                        const double* __restrict__ M1, const double* __restrict__ M2,
                                                        uint32_t n_fine, double w, double r0, double dr, double sigma,
                                                        float* __restrict__ h) {
+  griddep_wait();
+  griddep_launch();
   __shared__ double s_part[8];
   const uint32_t b = blockIdx.x;
   const double e0 = r0 + (double)b * dr, e1 = r0 + (double)(b + 1) * dr;
@@ -234,6 +238,8 @@ __global__ void __launch_bounds__(256) k_soft_finalize(const unsigned long long*
 __global__ void __launch_bounds__(256) k_soft_table(const float* __restrict__ G, uint32_t n_bins, uint32_t n_fine,
                                                     double w, double r0, double dr, double sigma,
                                                     float* __restrict__ T) {
+  griddep_wait();
+  griddep_launch();
   const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_fine) return;
   const double c = ((double)m + 0.5) * w;
@@ -258,6 +264,8 @@ __global__ void __launch_bounds__(256) k_soft_table(const float* __restrict__ G,
 // adjoint passes
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_soft_bwd(const SoftArgs a) {
+  griddep_wait();
+  griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
   __shared__ uint32_t s_rsrc[8][kSoftRuns], s_rpre[8][kSoftRuns + 1];
@@ -315,6 +323,8 @@ __global__ void __launch_bounds__(256) k_soft_bwd(const SoftArgs a) {
 // warp items (cell, first << 6 | count) over every non-empty cell of a list
 __global__ void __launch_bounds__(256) k_make_items(const uint32_t* __restrict__ count, Geo* geo,
                                                     uint2* __restrict__ item) {
+  griddep_wait();
+  griddep_launch();
   const uint32_t nc = geo->n_cells;
   const uint32_t lane = threadIdx.x & 31;
   for (uint32_t base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {
@@ -344,14 +354,20 @@ __global__ void __launch_bounds__(256) k_make_items(const uint32_t* __restrict__
 }
 
 __global__ void k_reset_items(Geo* geo) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) geo->work_n2 = 0, geo->work_n3 = 0, geo->work_next2 = 0;
 }
 
 __global__ void k_reset_counter(Geo* geo) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) geo->work_next2 = 0;
 }
 
 __global__ void k_soft_gs_out(const double* __restrict__ gs, float* __restrict__ out) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) *out = (float)*gs;
 }
 
@@ -394,7 +410,12 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   double w = 0.0;
   int rc = soft_setup(g, sigma, scale, bins, sa, w);
   if (rc) return rc;
-  rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s);
+  ZeroOut z;  // the moment accumulators are zeroed by the central-list reset kernel
+  z.p[0] = reinterpret_cast<uint64_t*>(g->soft_m0);
+  z.p[1] = reinterpret_cast<uint64_t*>(g->soft_m1);
+  z.p[2] = reinterpret_cast<uint64_t*>(g->soft_m2);
+  z.n[0] = z.n[1] = z.n[2] = sa.n_fine;
+  rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z);
   if (rc) return rc;
   sa.orec = g->ctr.rec;
   sa.ostart = g->ctr.start;
@@ -407,17 +428,14 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   sa.M0 = g->soft_m0;
   sa.M1 = g->soft_m1;
   sa.M2 = g->soft_m2;
-  PS_CUDA(cudaMemsetAsync(g->soft_m0, 0, (size_t)sa.n_fine * 8, s));
-  PS_CUDA(cudaMemsetAsync(g->soft_m1, 0, (size_t)sa.n_fine * 8, s));
-  PS_CUDA(cudaMemsetAsync(g->soft_m2, 0, (size_t)sa.n_fine * 8, s));
   const uint32_t smem = sa.n_fine * 12;
   int blocks = 0;
   rc = launch_grid_for(g, (const void*)k_soft_fwd, smem, &blocks);
   if (rc) return rc;
-  PS_LAUNCH(PS_KID_SOFT_FWD, s, k_soft_fwd<<<blocks, 256, smem, s>>>(sa));
+  PS_LAUNCH(PS_KID_SOFT_FWD, s, PS_CUDA(launch_pdl(k_soft_fwd, blocks, 256, smem, s, sa)));
   PS_LAUNCH(PS_KID_SOFT_FWD, s,
-            k_soft_finalize<<<bins.n_bins, 256, 0, s>>>(g->soft_m0, g->soft_m1, g->soft_m2, sa.n_fine, w, bins.r0,
-                                                        bins.dr, (double)sigma, d_h));
+            PS_CUDA(launch_pdl(k_soft_finalize, bins.n_bins, 256, 0, s, g->soft_m0, g->soft_m1, g->soft_m2, sa.n_fine, w, bins.r0,
+                                                        bins.dr, (double)sigma, d_h)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -434,8 +452,8 @@ int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
   PS_CUDA(cudaMemsetAsync(d_grad, 0, (size_t)g->n * 3 * sizeof(float), s));
   PS_CUDA(cudaMemsetAsync(g->soft_gs, 0, sizeof(double), s));
   PS_LAUNCH(PS_KID_SOFT_BWD, s,
-            k_soft_table<<<(sa.n_fine + 255) / 256, 256, 0, s>>>(d_G, bins.n_bins, sa.n_fine, w, bins.r0, bins.dr,
-                                                                 (double)sigma, g->soft_T));
+            PS_CUDA(launch_pdl(k_soft_table, (sa.n_fine + 255) / 256, 256, 0, s, d_G, bins.n_bins, sa.n_fine, w, bins.r0, bins.dr,
+                                                                 (double)sigma, g->soft_T)));
   sa.T = g->soft_T;
   sa.grad = d_grad;
   sa.grad_s = g->soft_gs;
@@ -453,10 +471,10 @@ int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
   sa.nstart = g->nbr.start;
   sa.ngeo = g->nbr.geo;
   sa.pass_b = 0;
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, k_soft_bwd<<<blocks, 256, smem, s>>>(sa));
+  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd, blocks, 256, smem, s, sa)));
   // pass B: owners = neighbours, candidates = centrals
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, k_reset_items<<<1, 32, 0, s>>>(g->nbr.geo));
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, k_make_items<<<g->num_sms * 4, 256, 0, s>>>(g->nbr.count, g->nbr.geo, g->nbr_witem));
+  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_reset_items, 1, 32, 0, s, g->nbr.geo)));
+  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_make_items, g->num_sms * 4, 256, 0, s, g->nbr.count, g->nbr.geo, g->nbr_witem)));
   sa.orec = g->nbr.rec;
   sa.ostart = g->nbr.start;
   sa.oitem = g->nbr_witem;
@@ -466,8 +484,8 @@ int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
   sa.nstart = g->ctr.start;
   sa.ngeo = g->nbr.geo;
   sa.pass_b = 1;
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, k_soft_bwd<<<blocks, 256, smem, s>>>(sa));
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, k_soft_gs_out<<<1, 32, 0, s>>>(g->soft_gs, d_grad_s));
+  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd, blocks, 256, smem, s, sa)));
+  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_gs_out, 1, 32, 0, s, g->soft_gs, d_grad_s)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
