@@ -260,6 +260,22 @@ PS_API int ps_rdf_soft_bwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mas
                            void* stream);
 
 /*
+ * Randomised type labels: the paper computes every statistic also for a
+ * random relabelling of the ions, as the reference for a random arrangement
+ * (Suppl. "Importance of high quality random number generators").
+ *   type_out[i] = type_in[perm(i)], perm a pseudo-random permutation of
+ *   [0, n) fixed by seed: a 4-round Feistel network on 2h bits (2^(2h) >= n,
+ *   h >= 1), round function = splitmix64 finaliser of (half-block + key_r),
+ *   key_r = finaliser(seed + (r + 1) * 0x9e3779b97f4a7c15), restricted to
+ *   [0, n) by cycle walking.  Label counts are kept exactly.
+ * type_in, type_out: device uint8 [n] (distinct); d_perm: optional device
+ * uint32 [n] receiving perm.  Run the statistics on type_out for the
+ * randomised companion.  n < 2^32.
+ */
+PS_API int ps_shuffle_labels(const uint8_t* type_in, uint8_t* type_out, int64_t n, uint64_t seed, uint32_t* d_perm,
+                             void* stream);
+
+/*
  * Allocation-free ps_build_grid + ps_spatstat.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * while they run the statistics, e.g. code running under CUDA stream capture
@@ -310,7 +326,8 @@ typedef enum {
   PS_KID_SOFT_FWD = 10,  /* smoothed RDF forward */
   PS_KID_SOFT_BWD = 11,  /* smoothed RDF adjoint */
   PS_KID_BATCH = 12,     /* batched sweep kernels */
-  PS_KID_COUNT_ = 13
+  PS_KID_LABELS = 13,    /* randomised labels */
+  PS_KID_COUNT_ = 14
 } ps_kernel_id;
 PS_API uint64_t ps_launch_count(void);
 PS_API int ps_prof_enable(uint32_t kid_mask);

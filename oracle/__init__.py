@@ -61,6 +61,10 @@ def _load():
         lib.orc_soft_fwd.restype = ctypes.c_int
         lib.orc_soft_bwd.argtypes = [P, P, P, i64, P, P, f32, f64, f64, f64, f64, u32, P, P, P]
         lib.orc_soft_bwd.restype = ctypes.c_int
+        lib.orc_label_perm.argtypes = [i64, ctypes.c_uint64, P]
+        lib.orc_label_perm.restype = None
+        lib.orc_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64]
+        lib.orc_shuffle_labels.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -163,3 +167,20 @@ def soft_bwd(xyz, type_, dsrf, ctr_types, nbr_types, dsrf_min, sigma, scale, r0,
     if rc != 0:
         raise RuntimeError(f"oracle soft_bwd failed: {rc}")
     return gx, float(gs[0])
+
+
+def label_perm(n: int, seed: int) -> np.ndarray:
+    """The pseudo-random permutation of [0, n) used for randomised labels (see oracle.c)."""
+    perm = np.empty(max(n, 1), np.uint32)
+    _load().orc_label_perm(int(n), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(perm))
+    return perm[:n]
+
+
+def shuffle_labels(type_, seed: int) -> np.ndarray:
+    """Randomised labels out[i] = type[perm(i)]."""
+    t = np.ascontiguousarray(type_, dtype=np.uint8)
+    out = np.empty_like(t)
+    rc = _load().orc_shuffle_labels(_ptr(t), _ptr(out), t.shape[0], int(seed) & 0xFFFFFFFFFFFFFFFF)
+    if rc != 0:
+        raise RuntimeError(f"oracle shuffle_labels failed: {rc}")
+    return out

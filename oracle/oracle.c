@@ -389,3 +389,53 @@ int orc_soft_bwd(const float* xyz, const uint8_t* type, const float* dsrf, int64
   return soft_pairs(xyz, type, dsrf, n, ctr_mask, nbr_mask, dsrf_min, sigma, scale, r0, dr, n_bins, G, NULL,
                     grad_xyz, grad_s);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Randomised type labels (Suppl. "Importance of high quality random number   */
+/* generators": every statistic is also computed for a random relabelling).   */
+/*                                                                            */
+/* The relabelling is out[i] = in[perm(i)] with perm a pseudo-random          */
+/* permutation of [0, n): a 4-round Feistel network over 2h bits              */
+/* (2^(2h) >= n, h >= 1) whose round function is the splitmix64 finaliser of  */
+/* (half-block + round key), round key r = finaliser(seed + (r + 1) * golden  */
+/* gamma), restricted to [0, n) by cycle walking (apply the network again      */
+/* until the value falls below n).                                            */
+/* ------------------------------------------------------------------------- */
+static uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+static uint64_t feistel(uint64_t x, const uint64_t key[4], unsigned h) {
+  const uint64_t mask = (h >= 64) ? ~0ULL : ((1ULL << h) - 1);
+  uint64_t L = x >> h, R = x & mask;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t t = L ^ (sm64_mix(R + key[r]) & mask);
+    L = R;
+    R = t;
+  }
+  return (L << h) | R;
+}
+
+void orc_label_perm(int64_t n, uint64_t seed, uint32_t* perm) {
+  unsigned h = 1;
+  while ((1ULL << (2 * h)) < (uint64_t)n) ++h;
+  uint64_t key[4];
+  for (int r = 0; r < 4; ++r) key[r] = sm64_mix(seed + (uint64_t)(r + 1) * 0x9e3779b97f4a7c15ULL);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t y = feistel((uint64_t)i, key, h);
+    while (y >= (uint64_t)n) y = feistel(y, key, h);
+    perm[i] = (uint32_t)y;
+  }
+}
+
+int orc_shuffle_labels(const uint8_t* in, uint8_t* out, int64_t n, uint64_t seed) {
+  if (n < 0 || n > 0xFFFFFFFFLL) return ORC_ERR_ARG;
+  uint32_t* perm = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
+  if (!perm) return ORC_ERR_OOM;
+  orc_label_perm(n, seed, perm);
+  for (int64_t i = 0; i < n; ++i) out[i] = in[perm[i]];
+  free(perm);
+  return ORC_OK;
+}

@@ -125,6 +125,7 @@ def lib():
     L.ps_batch_destroy.argtypes = [P]
     L.ps_rdf_soft_fwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P]
     L.ps_rdf_soft_bwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P, P, P]
+    L.ps_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
@@ -139,7 +140,7 @@ def _check(rc: int):
 
 
 KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
-           soft_bwd=11, batch=12)
+           soft_bwd=11, batch=12, labels=13)
 
 
 def launch_count() -> int:
@@ -456,3 +457,14 @@ class Batch:
                 _lib.ps_batch_destroy(self._h)
         except Exception:
             pass
+
+
+def shuffle_labels(type_, seed: int, with_perm: bool = False, stream=None):
+    """Randomised labels (ps_shuffle_labels): type_out[i] = type_[perm(i)]; returns type_out (and perm)."""
+    import torch
+
+    out = torch.empty_like(type_)
+    perm = torch.empty(type_.shape[0], dtype=torch.int32, device=type_.device) if with_perm else None
+    _check(lib().ps_shuffle_labels(_ptr(type_), _ptr(out), type_.shape[0], int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                   _ptr(perm), _stream(stream)))
+    return (out, perm) if with_perm else out
