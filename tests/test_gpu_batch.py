@@ -67,3 +67,32 @@ def test_batched_one_roi_against_oracle(ps, orc, spec):
             assert meta[0, p, 0, q, 0] == r["n_central"]
             np.testing.assert_array_equal(meta[0, p, 0, q, 4::2].astype(np.uint64), r["not_found"])
     b.close()
+
+
+def test_batched_256_rois_full_size_sampled(ps, spec):
+    """The full batched workload (256 ROIs, log-uniform 1e4..1e7 ions, k = 1..20, r_max {1,2,3} nm,
+    d_srf {0,1,2} nm, all-all / Sc-Sc / Al-Sc) in one run; 12 sampled (ROI, pair, r_max, d_srf)
+    records against the plain exact call, bit for bit."""
+    sizes = spec.roi_sizes(256)
+    rois = [tuple(torch.from_numpy(a).cuda() for a in spec.roi(i, n)) for i, n in enumerate(sizes)]
+    bins, rmax, dsrf = (0.0, 0.01, 300), [100, 200, 300], [0.0, 1.0, 2.0]
+    pairs, k_max = [("all", "all"), ([1], [1]), ([0], [1])], 20
+    b = ps.Batch(rois, bins, rmax, dsrf, pairs, k_max, 0.5)
+    out = b.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    picks = [(int(rng.integers(256)), int(rng.integers(3)), int(rng.integers(3)), int(rng.integers(3)))
+             for _ in range(12)]
+    picks.append((int(np.argmax(sizes)), 0, 2, 0))  # the largest ROI, all-all, r_max 3, d_srf >= 0
+    ks = list(range(1, k_max + 1))
+    for i, p, r, q in picks:
+        X, T, D = rois[i]
+        ctr, nbr = pairs[p]
+        g = ps.Grid(X.shape[0]).build(X, T, nbr, rmax[r] * 0.01 * (1 + 1e-6))
+        o = ps.spatstat(g, D, ctr, dsrf[q], (0.0, 0.01, rmax[r]), ks)
+        rdf, knn, meta = b.split(out[i, p, r, q].cpu().numpy())
+        np.testing.assert_array_equal(rdf[: rmax[r]], o["rdf"].cpu().numpy())
+        np.testing.assert_array_equal(knn[:, : rmax[r]], o["knn"].cpu().numpy())
+        np.testing.assert_array_equal(meta, o["meta"].cpu().numpy())
+        g.close()
+    b.close()

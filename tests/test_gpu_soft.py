@@ -139,3 +139,21 @@ def test_soft_gradient_vs_fp64_finite_differences_on_needle_subset(ps, orc, spec
     es = 1e-5
     fds = (loss(xyz, 1 + es) - loss(xyz, 1 - es)) / (2 * es)
     assert abs(gs - fds) <= 1e-4 * abs(fds)
+
+
+def test_soft_identities_on_1e7_needle(ps, spec):
+    """The full 1e7-ion needle of the smoothed-RDF workload: translation invariance and the scaling
+    identity of the adjoint, and h >= 0 summing to about the exact in-range pair count."""
+    xyz, t, d = spec.needle(spec.needle_10m_params())
+    G = np.random.default_rng(15).standard_normal(BINS[2])
+    h, gx, gs = _run(ps, xyz, t, d, "all", "all", 2.3, 1.0, G)
+    tot = np.abs(gx).sum()
+    assert np.all(np.abs(gx.sum(0)) <= 1e-4 * tot)
+    euler = float((xyz.astype(np.float64) * gx).sum())
+    assert abs(gs - euler) <= 1e-3 * abs(gs)
+    X, T, D = _dev(xyz, t, d)
+    g = ps.Grid(X.shape[0]).build(X, T, "all", 2.0)
+    o = ps.spatstat(g, D, "all", 2.3, BINS, [])
+    n_pairs = int(o["meta"][1].item())
+    assert h.min() >= 0 and abs(h.sum() - n_pairs) <= 2e-3 * n_pairs
+    g.close()
