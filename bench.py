@@ -73,6 +73,80 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+# FP32 pipe: 152 SMs x 128 lanes, one non-fused FP32 operation per lane per clock
+N_SM, FP32_LANES = 152, 128
+FLOPS_PER_CANDIDATE = 8  # d2 = ((dx*dx) + (dy*dy)) + (dz*dz): 3 sub, 3 mul, 2 add
+
+
+def alu_peak_tflops():
+    """FP32 (non-FMA) peak from the unit counts and the maximum SM clock."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return N_SM * FP32_LANES * mhz * 1e6 / 1e12, mhz
+
+
+def query_sources_sha256() -> str:
+    """Digest of the query kernels' sources: a stored ncu traffic figure holds only for this source."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("ps_query.cu", "ps_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_05188_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def stored_traffic(workload: str, kernel_config: dict):
+    """DRAM bytes per query launch from the committed ncu summary, or None when that summary was
+    taken on other kernel sources, another workload or another kernel configuration."""
+    p = os.path.join(ROOT, "profiles", "query_traffic_needle8m.md")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("record: "):
+                rec = json.loads(line[len("record: "):])
+                if (rec.get("workload") == workload and rec.get("source_sha256") == query_sources_sha256()
+                        and rec.get("kernel_config") == kernel_config):
+                    return float(rec["dram_bytes_per_launch"])
+    return None
+
+
+def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil):
+    """Central x candidate tests one query makes on this grid: for every central, the neighbour
+    records in the (2*stencil+1)^3 cells around its cell (clipped at the grid's faces).
+    Counted with plain torch ops from the grid geometry (reporting only, untimed)."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+
+    def lut(types):
+        m = ps.type_mask(types)
+        return torch.tensor([bool((int(m[t >> 6]) >> (t & 63)) & 1) for t in range(256)], device=T.device)
+
+    dims = info["dims"]
+    org = torch.tensor(info["origin"], dtype=torch.float32, device=X.device)
+    inv_h = float(np.float32(1.0 / float(info["cell"])))
+
+    def cells(P):
+        u = torch.floor((P - org) * inv_h).to(torch.int64)
+        for a in range(3):
+            u[:, a].clamp_(0, dims[a] - 1)
+        return (u[:, 2] * dims[1] + u[:, 1]) * dims[0] + u[:, 0]
+
+    Tl = T.long()
+    cnt = torch.bincount(cells(X[lut(nbr)[Tl]]), minlength=info["n_cells"]).view(dims[2], dims[1], dims[0])
+    s = int(stencil)
+    for ax in range(3):  # box sum of width 2s+1 along each axis (exact, int64)
+        c = torch.cumsum(torch.nn.functional.pad(cnt.movedim(ax, -1), (s + 1, s)), dim=-1)
+        cnt = (c[..., 2 * s + 1:] - c[..., : -(2 * s + 1)]).movedim(-1, ax)
+    cm = lut(ctr)[Tl] & (D >= dsrf_min)
+    return int(cnt.reshape(-1)[cells(X[cm])].sum().item())
+
+
 # ---------------------------------------------------------------------------
 # clocks sampling during the timed region
 # ---------------------------------------------------------------------------
@@ -474,8 +548,10 @@ def run_gpu(args, wl_name, wl):
         info = g.info()
         ctr_set = range(256) if ctr == "all" else ctr
         ntm = int(np.isin(t, list(ctr_set)).sum())
+        stencil = 1 if tuned[name]["cell_scale"] >= 1.0 else 2
         st["combos"].append(dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
-                                 n_ctr_typed=ntm, n_pairs=int(meta[1])))
+                                 n_ctr_typed=ntm, n_pairs=int(meta[1]),
+                                 candidates=candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil)))
         n_queries += int(meta[0])
         n_pairs += int(meta[1])
 
@@ -585,11 +661,28 @@ def run_gpu(args, wl_name, wl):
     per_launch_bytes = alg / launches_per_step
     avg_ms = dom_ms / max(1, dom_n)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                "avg_launch_us": avg_ms * 1e3, "launches": dom_n, "timing": "CUDA events around each launch, eager pass",
-                "time_share": shares[dom] / max(1e-12, sum(shares.values())),
-                "shares": {k: round(v / max(1e-12, sum(shares.values())), 4) for k, v in shares.items()}}
+    kcfg = {name: {"cell_scale": float(tuned[name]["cell_scale"]), "dense_min": int(tuned[name]["dense_min"])}
+            for name, _, _ in wl["combos"]}
+    common = {"kernel": dom, "peak_source": peak_kind, "avg_launch_us": avg_ms * 1e3, "launches": dom_n,
+              "timing": "CUDA events around each launch, eager pass",
+              "time_share": shares[dom] / max(1e-12, sum(shares.values())),
+              "shares": {k: round(v / max(1e-12, sum(shares.values())), 4) for k, v in shares.items()}}
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "algorithmic_bytes_per_launch": per_launch_bytes}
+    if dom == "query":
+        # the pair test is the work: FP32 arithmetic on L2-resident records (DRAM traffic is a few MB)
+        cands = sum(c["candidates"] for c in st["combos"])
+        flops = FLOPS_PER_CANDIDATE * cands / launches_per_step
+        alu_peak, mhz = alu_peak_tflops()
+        alu = flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu / alu_peak,
+                    "traffic": stored_traffic(wl_name, kcfg), "traffic_unit": "DRAM bytes per launch (ncu)",
+                    "flops_per_launch": flops, "candidate_tests_per_step": cands,
+                    "peak_derivation": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz, 1 op/lane/clock",
+                    "hbm": hbm, **common}
+    else:
+        roofline = {"bound": "hbm", **{k: v for k, v in hbm.items() if k != "algorithmic_bytes_per_launch"},
+                    "traffic": None, **common}
 
     forms = None
     if rank == 0 and not args.no_forms:

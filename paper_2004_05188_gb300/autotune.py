@@ -35,12 +35,20 @@ def signature(n: int, n_nbr: int, n_ctr: int, bins, ks) -> str:
     return f"n{p2(n)}-nb{p2(n_nbr)}-nc{p2(n_ctr)}-r{r0 + dr * nb:.3f}-k{max(ks) if ks else 0}"
 
 
-def choose(timings: dict):
-    """The fastest configuration; ties go to the earlier candidate."""
+MARGIN = 0.08  # another configuration replaces the first only when it is this much faster
+
+
+def choose(timings: dict, margin: float = MARGIN):
+    """The fastest configuration; ties go to the earlier candidate, and the first candidate (the
+    default, 27-cell search on the warp kernel) stays unless another beats it by more than
+    `margin` of its time, so that timing noise does not flip the configuration between runs."""
     best = None
     for cfg, ms in timings.items():
         if best is None or ms < timings[best]:
             best = cfg
+    first = next(iter(timings), None)
+    if first is not None and timings[best] > timings[first] * (1.0 - margin):
+        return first
     return best
 
 

@@ -16,6 +16,13 @@ def test_choose_fastest_and_ties():
     assert autotune.choose({(1.0, 0): 1.0, (0.5, 0): 1.0}) == (1.0, 0)
 
 
+def test_choose_keeps_default_within_margin():
+    # 4.8 % faster is within the 8 % margin: the default stays; 10 % faster replaces it
+    assert autotune.choose({(1.0, 0): 0.3045, (0.5, 0): 0.3718, (1.0, 128): 0.29}) == (1.0, 0)
+    assert autotune.choose({(1.0, 0): 1.0, (0.5, 0): 0.9, (1.0, 128): 0.95}) == (0.5, 0)
+    assert autotune.choose({(1.0, 0): 1.0, (0.5, 0): 0.97}, margin=0.0) == (0.5, 0)
+
+
 def test_tune_uses_runner_and_caches(tmp_path):
     calls = []
 
