@@ -10,6 +10,9 @@ the kNN and RDF statistics (Methods, "Descriptive, two-point spatial
 statistics, and clustering"; Suppl. Figs. SchematicKNN/SchematicRDF), with
 the d_srf edge rule (Methods, "Ion-to-edge distancing") and per-ROI
 enumeration (Suppl., "Customized user defined batch processing queues").
+The spatial distribution map (the 3-D two-point statistic, same Methods
+passage; voxelised displacements within the ROI radius R, Results on strong
+scaling) bins the float32 displacement of every in-range pair.
 The smoothed-RDF functions are FP64.  Parity for the g(r) normalisation
 constants is unpinned (the paper gives no formula); everything else is
 pinned by the tests under tests/test_oracle_*.py.
@@ -61,6 +64,10 @@ def _load():
         lib.orc_soft_fwd.restype = ctypes.c_int
         lib.orc_soft_bwd.argtypes = [P, P, P, i64, P, P, f32, f64, f64, f64, f64, u32, P, P, P]
         lib.orc_soft_bwd.restype = ctypes.c_int
+        lib.orc_sdm_edges.argtypes = [f64, u32, P]
+        lib.orc_sdm_edges.restype = None
+        lib.orc_sdm.argtypes = [P, P, P, i64, P, P, f32, f64, f64, u32, P, P]
+        lib.orc_sdm.restype = ctypes.c_int
         lib.orc_label_perm.argtypes = [i64, ctypes.c_uint64, P]
         lib.orc_label_perm.restype = None
         lib.orc_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64]
@@ -167,6 +174,27 @@ def soft_bwd(xyz, type_, dsrf, ctr_types, nbr_types, dsrf_min, sigma, scale, r0,
     if rc != 0:
         raise RuntimeError(f"oracle soft_bwd failed: {rc}")
     return gx, float(gs[0])
+
+
+def sdm_edges(w: float, n_vox: int) -> np.ndarray:
+    """Voxel edges V[m] = (float)((m - n_vox/2) * w), m = 0..n_vox (see oracle.c)."""
+    V = np.empty(n_vox + 1, dtype=np.float32)
+    _load().orc_sdm_edges(float(w), int(n_vox), _ptr(V))
+    return V
+
+
+def sdm(xyz, type_, dsrf, ctr_types, nbr_types, dsrf_min, r_max, w, n_vox):
+    """Spatial distribution map H[n_vox, n_vox, n_vox] (indexed [mz, my, mx]) and
+    meta = {n_central, pairs in the map, pairs outside the voxel cube}."""
+    xyz, type_, dsrf, n = _prep(xyz, type_, dsrf)
+    H = np.zeros((n_vox, n_vox, n_vox), np.uint64)
+    meta = np.zeros(3, np.uint64)
+    rc = _load().orc_sdm(_ptr(xyz), _ptr(type_), _ptr(dsrf), n, _ptr(type_mask(ctr_types)),
+                         _ptr(type_mask(nbr_types)), float(dsrf_min), float(r_max), float(w), int(n_vox), _ptr(H),
+                         _ptr(meta))
+    if rc != 0:
+        raise RuntimeError(f"oracle sdm failed: {rc}")
+    return H, meta
 
 
 def label_perm(n: int, seed: int) -> np.ndarray:

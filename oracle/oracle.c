@@ -29,7 +29,10 @@
  *     fewer than k of them is "not found";
  *   - smoothed RDF: each pair spreads a Gaussian of width sigma, integrated
  *     over every bin (the rectangular transfer function convolved with a
- *     Gaussian), over the pairs with s*d < stop + 6 sigma.
+ *     Gaussian), over the pairs with s*d < stop + 6 sigma;
+ *   - spatial distribution map: the pairs with d2 < (float)(R*R) binned by
+ *     their float32 displacement x_j - x_i into cubic voxels, edges
+ *     V[m] = (float)((m - n_vox/2) * w), half-open on every axis.
  *
  * Status codes: 0 ok, 1 bad argument, 2 out of memory.
  */
@@ -309,6 +312,122 @@ int orc_central_brute(const float* xyz, const uint8_t* type, int64_t n, int64_t 
   free(L.v);
   free(E);
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Spatial distribution map: the three-dimensional two-point statistic of     */
+/* which RDF and kNN are annular integrals (Methods, "Descriptive, two-point  */
+/* spatial statistics, and clustering"; Results, strong scaling: cubic voxels */
+/* about each central ion, ROI radius R).                                     */
+/*                                                                            */
+/*  for every central i and neighbour j != i with d2_ij < (float)(R*R):        */
+/*     the displacement (dx, dy, dz) = x_j - x_i (float32, as for d2) falls    */
+/*     in voxel (mx, my, mz) with V[m] <= d < V[m+1] on each axis,             */
+/*     V[m] = (float)((m - n_vox/2) * w) in double, m = 0..n_vox;              */
+/*     H[(mz*n_vox + my)*n_vox + mx] += 1.  A displacement outside the cube    */
+/*     [V[0], V[n_vox])^3 is counted in meta[2] instead.                       */
+/*  meta = {n_central, pairs in the map, pairs outside the cube}.             */
+/* ------------------------------------------------------------------------- */
+void orc_sdm_edges(double w, uint32_t n_vox, float* V) {
+  for (uint32_t m = 0; m <= n_vox; ++m) V[m] = (float)(((double)m - (double)n_vox / 2.0) * w);
+}
+
+/* voxel index along one axis: the m in [0, n) with V[m] <= d < V[m+1]; -1 outside [V[0], V[n]) */
+static int64_t vox_of(const float* V, uint32_t n, float d) {
+  if (!(d >= V[0]) || !(d < V[n])) return -1;
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (d >= V[mid])
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+int orc_sdm(const float* xyz, const uint8_t* type, const float* dsrf, int64_t n, const uint64_t* ctr_mask,
+            const uint64_t* nbr_mask, float dsrf_min, double r_max, double w, uint32_t n_vox, uint64_t* H,
+            uint64_t* meta) {
+  if (n < 0 || !(r_max > 0) || !(w > 0) || n_vox == 0 || n_vox > 1024) return ORC_ERR_ARG;
+  const size_t nh = (size_t)n_vox * n_vox * n_vox;
+  memset(H, 0, nh * sizeof(uint64_t));
+  meta[0] = meta[1] = meta[2] = 0;
+  float* V = (float*)malloc((size_t)(n_vox + 1) * sizeof(float));
+  if (!V) return ORC_ERR_OOM;
+  orc_sdm_edges(w, n_vox, V);
+  const float ER = (float)(r_max * r_max);
+  /* cell list of the neighbour set, cells of edge just above R */
+  const double h = sqrt((double)ER) * (1.0 + 1e-5) + 1e-6;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int64_t nn = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    if (!in_mask(nbr_mask, type[j])) continue;
+    ++nn;
+    for (int a = 0; a < 3; ++a) {
+      if (xyz[3 * j + a] < lo[a]) lo[a] = xyz[3 * j + a];
+      if (xyz[3 * j + a] > hi[a]) hi[a] = xyz[3 * j + a];
+    }
+  }
+  int64_t dim[3] = {1, 1, 1};
+  if (nn > 0)
+    for (int a = 0; a < 3; ++a) dim[a] = (int64_t)floor((hi[a] - lo[a]) / h) + 1;
+  else
+    lo[0] = lo[1] = lo[2] = 0.0;
+  const int64_t ncell = dim[0] * dim[1] * dim[2];
+  int64_t* start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+  int64_t* item = (int64_t*)malloc((size_t)(nn > 0 ? nn : 1) * sizeof(int64_t));
+  int64_t* fill = (int64_t*)calloc((size_t)ncell, sizeof(int64_t));
+  int rc = ORC_OK;
+  if (!start || !item || !fill) {
+    rc = ORC_ERR_OOM;
+    goto done;
+  }
+#define CELLS(x, a) ((int64_t)fmin(fmax(floor(((double)(x) - lo[a]) / h), 0.0), (double)(dim[a] - 1)))
+  for (int64_t j = 0; j < n; ++j) {
+    if (!in_mask(nbr_mask, type[j])) continue;
+    start[(CELLS(xyz[3 * j + 2], 2) * dim[1] + CELLS(xyz[3 * j + 1], 1)) * dim[0] + CELLS(xyz[3 * j], 0) + 1] += 1;
+  }
+  for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+  for (int64_t j = 0; j < n; ++j) {
+    if (!in_mask(nbr_mask, type[j])) continue;
+    const int64_t c = (CELLS(xyz[3 * j + 2], 2) * dim[1] + CELLS(xyz[3 * j + 1], 1)) * dim[0] + CELLS(xyz[3 * j], 0);
+    item[start[c] + fill[c]++] = j;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (!in_mask(ctr_mask, type[i]) || !(dsrf[i] >= dsrf_min)) continue;
+    meta[0] += 1;
+    const float* xi = xyz + 3 * i;
+    const int64_t cx = CELLS(xi[0], 0), cy = CELLS(xi[1], 1), cz = CELLS(xi[2], 2);
+    for (int64_t z = cz - 1; z <= cz + 1; ++z)
+      for (int64_t y = cy - 1; y <= cy + 1; ++y)
+        for (int64_t x = cx - 1; x <= cx + 1; ++x) {
+          if (x < 0 || y < 0 || z < 0 || x >= dim[0] || y >= dim[1] || z >= dim[2]) continue;
+          const int64_t c = (z * dim[1] + y) * dim[0] + x;
+          for (int64_t t = start[c]; t < start[c + 1]; ++t) {
+            const int64_t j = item[t];
+            if (j == i) continue;
+            const float* xj = xyz + 3 * j;
+            if (!(dist2(xi, xj) < ER)) continue;
+            const int64_t mx = vox_of(V, n_vox, xj[0] - xi[0]);
+            const int64_t my = vox_of(V, n_vox, xj[1] - xi[1]);
+            const int64_t mz = vox_of(V, n_vox, xj[2] - xi[2]);
+            if (mx < 0 || my < 0 || mz < 0) {
+              meta[2] += 1;
+            } else {
+              H[((size_t)mz * n_vox + (size_t)my) * n_vox + (size_t)mx] += 1;
+              meta[1] += 1;
+            }
+          }
+        }
+  }
+#undef CELLS
+done:
+  free(fill);
+  free(item);
+  free(start);
+  free(V);
+  return rc;
 }
 
 /* ------------------------------------------------------------------------- */
