@@ -375,6 +375,58 @@ def measure_soft(args, dev):
             "timing": "CUDA events, eager, grid build included in fwd and plain"}
 
 
+def measure_sdm(args, dev):
+    """Spatial distribution maps on the 8.07e6-ion needle with the paper's strong-scaling setting
+    (ROI radius 2 nm, cubic voxels of edge 0.025 nm: 160^3 voxels), d_srf >= 2 nm: Sc-Sc and
+    all-all, each grid build + map against the plain exact RDF over the same pairs."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+
+    xyz, t, d = make_cloud("needle8m")
+    N = xyz.shape[0]
+    X = torch.from_numpy(xyz).to(dev)
+    T = torch.from_numpy(t).to(dev)
+    D = torch.from_numpy(d).to(dev)
+    R, w, nv, dmin = 2.0, 0.025, 160, 2.0
+    bins = (0.0, R, 1)
+    g = ps.Grid(N)
+    res = {"workload": f"needle {N} ions, ROI radius {R} nm, voxel {w} nm ({nv}^3), d_srf>={dmin} nm",
+           "timing": "CUDA events, eager, grid build included, best of 3"}
+    for name, types in (("Sc-Sc", [1]), ("all-all", "all")):
+        out = ps.sdm(g.build(X, T, types, R), D, types, dmin, R, w, nv)
+        plain_out = ps.spatstat(g, D, types, dmin, bins, [], rdf=True)
+
+        def run_sdm():
+            g.build(X, T, types, R)
+            ps.sdm(g, D, types, dmin, R, w, nv, out=out)
+
+        def run_plain():
+            g.build(X, T, types, R)
+            ps.spatstat(g, D, types, dmin, bins, [], rdf=True, out=plain_out, check=False)
+
+        times = {}
+        for key, fn in (("sdm", run_sdm), ("plain", run_plain)):
+            fn()
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+            times[key] = best
+        meta = out["meta"].cpu().numpy()
+        if meta[3] != 0 or int(meta[1]) != int(plain_out["meta"][1].item()):
+            raise RuntimeError(f"SDM {name}: status {meta[3]} or pair count differs from the RDF")
+        res[name] = {"n_central": int(meta[0]), "pairs": int(meta[1]), "sdm_ms": times["sdm"],
+                     "plain_rdf_ms": times["plain"], "sdm_pairs_per_s": int(meta[1]) / (times["sdm"] * 1e-3),
+                     "sdm_over_plain": times["sdm"] / times["plain"]}
+    g.close()
+    return res
+
+
 def measure_batched(args, dev):
     """256 ROIs (needles and cylinders, log-uniform 1e4..1e7 ions), each with the sweep
     k = 1..20, r_max in {1, 2, 3} nm (0.01 nm bins), d_srf >= {0, 1, 2} nm, type pairs
@@ -689,6 +741,7 @@ def run_gpu(args, wl_name, wl):
         forms = {"soft": measure_soft(args, dev)}
         if args.batch_rois > 0:
             forms["batched"] = measure_batched(args, dev)
+        forms["sdm"] = measure_sdm(args, dev)
 
     # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
@@ -745,7 +798,8 @@ def main():
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
     ap.add_argument("--no-autotune", action="store_true", help="use --cell-scale/--dense-min instead of the autotuner")
-    ap.add_argument("--only-form", choices=["soft", "batched"], help="measure only this form (no exact step line)")
+    ap.add_argument("--only-form", choices=["soft", "batched", "sdm"],
+                    help="measure only this form (no exact step line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     wl = dict(WORKLOADS[args.workload])
@@ -761,7 +815,7 @@ def main():
 
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
-        fn = {"soft": measure_soft, "batched": measure_batched}[args.only_form]
+        fn = {"soft": measure_soft, "batched": measure_batched, "sdm": measure_sdm}[args.only_form]
         print(json.dumps({"form": args.only_form, **fn(args, dev)}), flush=True)
         return 0
     return run_gpu(args, args.workload, wl)

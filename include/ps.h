@@ -260,6 +260,33 @@ PS_API int ps_rdf_soft_bwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mas
                            void* stream);
 
 /*
+ * Spatial distribution map: the three-dimensional two-point statistic (Methods,
+ * "Descriptive, two-point spatial statistics, and clustering": RDF and kNN are
+ * its annular integrals; Results on strong scaling: cubic voxels of
+ * (0.025 nm)^3 about every central ion, ROI radius R = 2 nm).
+ *   For every central i (type in ctr_mask, d_srf >= dsrf_min) and neighbour
+ *   j != i of the grid's set with d2_ij < (float)(r_max^2), the float32
+ *   displacement (dx, dy, dz) = x_j - x_i lands in voxel (mx, my, mz) with
+ *   V[m] <= d < V[m+1] on each axis, V[m] = (float)((m - n_vox/2) * w)
+ *   computed in double, m = 0..n_vox.
+ *   g        grid built with r_cut >= r_max (else PS_ERR_INVALID_ARG)
+ *   spec     r_max > 0, w > 0, 1 <= n_vox <= PS_SDM_MAX_VOX
+ *   d_hist   device uint64 [n_vox][n_vox][n_vox], index (mz*n_vox + my)*n_vox + mx
+ *   d_meta   device uint64 [PS_SDM_META_LEN]: n_central, pairs in the map,
+ *            pairs whose displacement lies outside the voxel cube, status
+ * Both outputs are overwritten.  Asynchronous on `stream`.
+ */
+#define PS_SDM_MAX_VOX 1024
+#define PS_SDM_META_LEN 4
+typedef struct {
+  double r_max; /* ROI radius (nm) */
+  double w;     /* voxel edge (nm) */
+  uint32_t n_vox;
+} ps_sdm_spec;
+PS_API int ps_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_sdm_spec spec,
+                  uint64_t* d_hist, uint64_t* d_meta, void* stream);
+
+/*
  * Randomised type labels: the paper computes every statistic also for a
  * random relabelling of the ions, as the reference for a random arrangement
  * (Suppl. "Importance of high quality random number generators").
@@ -327,7 +354,8 @@ typedef enum {
   PS_KID_SOFT_BWD = 11,  /* smoothed RDF adjoint */
   PS_KID_BATCH = 12,     /* batched sweep kernels */
   PS_KID_LABELS = 13,    /* randomised labels */
-  PS_KID_COUNT_ = 14
+  PS_KID_SDM = 14,       /* spatial distribution map */
+  PS_KID_COUNT_ = 15
 } ps_kernel_id;
 PS_API uint64_t ps_launch_count(void);
 PS_API int ps_prof_enable(uint32_t kid_mask);

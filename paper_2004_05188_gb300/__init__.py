@@ -81,6 +81,10 @@ class Dataset(ctypes.Structure):
     _fields_ = [("xyz", ctypes.c_void_p), ("type", ctypes.c_void_p), ("dsrf", ctypes.c_void_p), ("n", ctypes.c_int64)]
 
 
+class SdmSpec(ctypes.Structure):
+    _fields_ = [("r_max", ctypes.c_double), ("w", ctypes.c_double), ("n_vox", ctypes.c_uint32)]
+
+
 class Sweep(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("bins", Bins), ("n_rmax", ctypes.c_uint32),
                 ("rmax_bins", ctypes.c_uint32 * 4), ("n_dsrf", ctypes.c_uint32), ("dsrf_min", ctypes.c_float * 4),
@@ -126,6 +130,7 @@ def lib():
     L.ps_rdf_soft_fwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P]
     L.ps_rdf_soft_bwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P, P, P]
     L.ps_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64, P, P]
+    L.ps_sdm.argtypes = [P, P, P, f32, SdmSpec, P, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
@@ -140,7 +145,7 @@ def _check(rc: int):
 
 
 KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
-           soft_bwd=11, batch=12, labels=13)
+           soft_bwd=11, batch=12, labels=13, sdm=14)
 
 
 def launch_count() -> int:
@@ -313,6 +318,24 @@ def rdf_hist(grid: Grid, dsrf, ctr_types, dsrf_min: float, bins, stream=None):
     _check(lib().ps_rdf_hist(grid.handle, _ptr(dsrf), mp, float(dsrf_min), Bins(r0, dr, nb), _ptr(h), _ptr(meta),
                              _stream(stream)))
     return h, meta
+
+
+SDM_META_LEN = 4
+
+
+def sdm(grid: Grid, dsrf, ctr_types, dsrf_min: float, r_max: float, w: float, n_vox: int, out=None, stream=None):
+    """Spatial distribution map (ps_sdm): returns {"H": int64 [n_vox, n_vox, n_vox] indexed [mz, my, mx],
+    "meta": int64 [4] = n_central, pairs in the map, pairs outside the voxel cube, status}."""
+    import torch
+
+    dev = grid._refs[0].device
+    if out is None:
+        out = dict(H=torch.empty((n_vox, n_vox, n_vox), dtype=torch.int64, device=dev),
+                   meta=torch.empty(SDM_META_LEN, dtype=torch.int64, device=dev))
+    m, mp = _mask_ptr(ctr_types)
+    _check(lib().ps_sdm(grid.handle, _ptr(dsrf), mp, float(dsrf_min), SdmSpec(float(r_max), float(w), int(n_vox)),
+                        _ptr(out["H"]), _ptr(out["meta"]), _stream(stream)))
+    return out
 
 
 def soft_rdf_fwd(grid: Grid, dsrf, ctr_types, dsrf_min: float, sigma: float, scale: float, bins, out=None,

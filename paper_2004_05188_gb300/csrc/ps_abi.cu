@@ -237,6 +237,20 @@ int ps_spatstat(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float
                    static_cast<cudaStream_t>(stream));
 }
 
+int ps_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_sdm_spec spec,
+           uint64_t* d_hist, uint64_t* d_meta, void* stream) {
+  if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "ps_sdm: grid is NULL or not built");
+  if (!ctr_mask || !d_hist || !d_meta) return fail(PS_ERR_INVALID_ARG, "ps_sdm: ctr_mask/d_hist/d_meta is NULL");
+  if (std::isnan(dsrf_min)) return fail(PS_ERR_INVALID_ARG, "ps_sdm: dsrf_min is NaN");
+  if (!(spec.r_max > 0.0) || !std::isfinite(spec.r_max) || !(spec.w > 0.0) || !std::isfinite(spec.w))
+    return fail(PS_ERR_INVALID_ARG, "ps_sdm: r_max and w must be positive and finite");
+  if (spec.n_vox < 1 || spec.n_vox > PS_SDM_MAX_VOX) return fail(PS_ERR_UNSUPPORTED, "ps_sdm: n_vox must be in [1, 1024]");
+  const float ER = (float)(spec.r_max * spec.r_max);
+  if ((double)ER > (double)g->r_cut * (double)g->r_cut)
+    return fail(PS_ERR_INVALID_ARG, "ps_sdm: the grid's r_cut is below r_max");
+  return run_sdm(g, dsrf, ctr_mask, dsrf_min, spec, d_hist, d_meta, static_cast<cudaStream_t>(stream));
+}
+
 static int check_soft(ps_grid* g, const uint64_t* ctr_mask, ps_bins bins, float dsrf_min) {
   if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "smoothed RDF: grid is NULL or not built");
   if (!ctr_mask) return fail(PS_ERR_INVALID_ARG, "smoothed RDF: ctr_mask is NULL");

@@ -10,7 +10,7 @@
 //
 // Pipeline (all on the device, no host synchronisation):
 //   reset -> select + bounding box -> geometry + zero counts -> count ranks
-//   -> exclusive scan (tiles, tile prefixes, apply) -> scatter
+//   -> single-pass exclusive scan (decoupled look-back) -> scatter
 // The selection kernels read 16 type labels per thread (one 16-byte load).
 #include <cstring>
 
@@ -52,6 +52,36 @@ __device__ __forceinline__ uint32_t warp_append_n(uint32_t cnt, uint32_t* counte
   return base + x - cnt;
 }
 
+// block-aggregated append of `cnt` items per thread (every thread of the block
+// calls it): one atomic per block instead of one per warp, since appends from
+// all warps of the grid to one counter serialise at its L2 slice.  Returns this
+// thread's first slot.  s_w and s_x are per-block scratch of blockDim/32 words.
+__device__ __forceinline__ uint32_t block_append_n(uint32_t cnt, uint32_t* counter, uint32_t* s_w, uint32_t* s_x,
+                                                   uint32_t* s_base) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = lane < nw ? s_w[lane] : 0u;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
+    }
+    if (lane < nw) s_x[lane] = inc - v;
+    if (lane == 31) *s_base = inc ? atomicAdd(counter, inc) : 0u;
+  }
+  __syncthreads();
+  return *s_base + s_x[warp] + x - cnt;
+}
+
 // the 16 type labels of group g (ions 16g .. 16g+15); `valid` masks the labels past n
 __device__ __forceinline__ void load_types16(const uint8_t* __restrict__ type, int64_t n, int64_t g, bool vec,
                                              uint8_t (&t)[kGroup], uint32_t& valid) {
@@ -80,7 +110,7 @@ __global__ void k_reset(Geo* geo) {
     geo->n_sel = 0;
     geo->status = 0;
     geo->work_n = geo->work_n2 = geo->work_n3 = 0;
-    geo->work_next = geo->work_next2 = 0;
+    geo->work_next = geo->work_next2 = geo->work_next3 = 0;
   }
 }
 
@@ -100,6 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_select_bbox(const float* __restric
                                                           Geo* geo) {
   griddep_wait();
   griddep_launch();
+  __shared__ uint32_t s_aw[kThreads / 32], s_ax[kThreads / 32], s_abase;
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
   const int64_t groups = (n + kGroup - 1) / kGroup;
@@ -116,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_select_bbox(const float* __restric
       m &= valid;
     }
     const uint32_t cnt = __popc(m);
-    uint32_t slot = warp_append_n(cnt, &geo->n_sel);
+    uint32_t slot = block_append_n(cnt, &geo->n_sel, s_aw, s_ax, &s_abase);
     const int64_t i0 = g * kGroup;
     if (cnt >= 4 && vec && m == 0xFFFFu) {
       // a full group: read its 192 bytes of coordinates as 12 float4
@@ -250,6 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_central_select_count(const float* 
                                                                    uint32_t* __restrict__ sel, uint2* __restrict__ cr) {
   griddep_wait();
   griddep_launch();
+  __shared__ uint32_t s_aw[kThreads / 32], s_ax[kThreads / 32], s_abase;
   const Geo g = *ngeo;
   bool bad = false;
   const int64_t groups = (n + kGroup - 1) / kGroup;
@@ -288,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) k_central_select_count(const float* 
         m &= keep;
       }
     }
-    uint32_t slot = warp_append_n(__popc(m), &cgeo->n_sel);
+    uint32_t slot = block_append_n(__popc(m), &cgeo->n_sel, s_aw, s_ax, &s_abase);
     while (m) {
       const int k = __ffs(m) - 1;
       m &= m - 1;
@@ -315,7 +347,7 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     cgeo->n_sel = 0;
     cgeo->status = 0;
     cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = 0;
-    cgeo->work_next = cgeo->work_next2 = 0;
+    cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
   }
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (uint32_t c = tid; c < nc; c += stride) count[c] = 0;
@@ -352,6 +384,22 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return prefix + x - v;
 }
 
+// Candidates of cell c: the neighbour records in the cells within `st` cells of it.
+__device__ __forceinline__ uint32_t stencil_count(const uint32_t* __restrict__ nstart, const Geo* g, uint32_t c, int st) {
+  const uint32_t d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
+  const uint32_t cx = c % d0, cy = (c / d0) % d1, cz = c / (d0 * d1);
+  const uint32_t xlo = cx >= (uint32_t)st ? cx - st : 0, xhi = cx + st < d0 ? cx + st : d0 - 1;
+  const int ylo = max((int)cy - st, 0), yhi = min((int)cy + st, (int)d1 - 1);
+  const int zlo = max((int)cz - st, 0), zhi = min((int)cz + st, (int)d2 - 1);
+  uint32_t n = 0;
+  for (int z = zlo; z <= zhi; ++z)
+    for (int y = ylo; y <= yhi; ++y) {
+      const uint32_t row = ((uint32_t)z * d1 + (uint32_t)y) * d0;
+      n += nstart[row + xhi + 1] - nstart[row + xlo];
+    }
+  return n;
+}
+
 // Warp items of a cell with n centrals: n <= 3 gives one item (the lanes of
 // the warp split the candidates of each central); otherwise ceil(n/32)
 // balanced batches of at most 32 centrals (one lane per central).
@@ -376,12 +424,14 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 // look-back words for the next scan.  Also writes the end sentinel and, for the
 // central list, the work lists: cells with at least dense_min centrals go to
 // `work` (CTA kernel), the others are split into warp items (cell,
-// first << 6 | count), cells with at least kHeavy centrals from the front of
-// `witem`, the rest from the back.
+// first << 6 | count): sparse cells (fewer than kHeavy centrals and at most
+// kSparseCand candidates in the stencil of the neighbour grid `nstart`) from
+// the back of `witem`, the rest from the front.
 __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ count, Geo* geo,
                                                        uint32_t* __restrict__ start, uint32_t* __restrict__ work,
                                                        uint2* __restrict__ witem, uint32_t dense_min, uint32_t cap,
-                                                       unsigned long long* state, uint32_t* ctr) {
+                                                       unsigned long long* state, uint32_t* ctr,
+                                                       const uint32_t* __restrict__ nstart, int stencil) {
   griddep_wait();
   griddep_launch();
   __shared__ uint32_t s_warp[32];
@@ -402,31 +452,49 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
     }
     uint32_t total;
     const uint32_t excl = block_exclusive_scan(sum, s_warp, total);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // warp 0 looks back 32 predecessors at a time: lane l reads tile j - l; the
+      // window is summed up to the nearest tile that holds an inclusive prefix
+      // (the virtual tile -1 holds prefix 0)
+      const uint32_t lane = lane_id();
       uint32_t prefix = 0;
       if (t > 0) {
-        st_release(&state[t], kFlagA | total);
+        if (lane == 0) st_release(&state[t], kFlagA | total);
         int j = (int)t - 1;
         uint64_t t0 = 0;
         while (j >= 0) {
-          const unsigned long long w = ld_acquire(&state[j]);
-          if ((w >> 62) == 0) {
-            if (t0 == 0) t0 = global_ns();
-            if (global_ns() - t0 > kWaitLimitNs) {
-              atomicCAS(&geo->status, 0, (int)PS_ERR_TIMEOUT);
+          const int idx = j - (int)lane;
+          const unsigned long long w = idx >= 0 ? ld_acquire(&state[idx]) : kFlagP;
+          const uint32_t isP = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+          const uint32_t notready = __ballot_sync(0xffffffffu, (w >> 62) == 0);
+          const uint32_t lim = isP ? (uint32_t)(__ffs(isP) - 1) : 31u;
+          const uint32_t need = lim == 31u ? 0xffffffffu : ((2u << lim) - 1u);
+          if (notready & need) {
+            int give_up = 0;
+            if (lane == 0) {
+              if (t0 == 0) t0 = global_ns();
+              give_up = global_ns() - t0 > kWaitLimitNs;
+            }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) {
+              if (lane == 0) atomicCAS(&geo->status, 0, (int)PS_ERR_TIMEOUT);
               break;
             }
             continue;
           }
-          prefix += (uint32_t)w;
-          if ((w >> 62) == 2) break;
-          --j;
+          uint32_t v = lane <= lim ? (uint32_t)w : 0u;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          prefix += v;
+          if (isP) break;
+          j -= 32;
           t0 = 0;
         }
       }
-      st_release(&state[t], kFlagP | (uint32_t)(prefix + total));
-      s_prefix = prefix;
-      if (t == tiles - 1) start[nc] = prefix + total;  // end sentinel: number of records
+      if (lane == 0) {
+        st_release(&state[t], kFlagP | (uint32_t)(prefix + total));
+        s_prefix = prefix;
+        if (t == tiles - 1) start[nc] = prefix + total;  // end sentinel: number of records
+      }
     }
     __syncthreads();
     uint32_t run = s_prefix + excl;
@@ -436,16 +504,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
       run += v[k];
     }
     if (work != nullptr) {
-      uint32_t n_heavy = 0, n_light = 0;
+      uint32_t n_front = 0, n_back = 0;
+      bool sparse[kScanItems];
 #pragma unroll
       for (int k = 0; k < kScanItems; ++k) {
         const bool dense = (c0 + k < nc) && v[k] >= dense_min;
         const uint32_t s1 = warp_append(dense, &geo->work_n);
         if (dense) work[s1] = c0 + k;
-        if (!dense) (v[k] >= kHeavy ? n_heavy : n_light) += items_of(v[k]);
+        sparse[k] = !dense && v[k] > 0 && v[k] < kHeavy && nstart != nullptr &&
+                    stencil_count(nstart, geo, c0 + k, stencil) <= kSparseCand;
+        if (!dense) (sparse[k] ? n_back : n_front) += items_of(v[k]);
       }
-      uint32_t hs = warp_append_n(n_heavy, &geo->work_n2);
-      uint32_t ls = warp_append_n(n_light, &geo->work_n3);
+      uint32_t hs = warp_append_n(n_front, &geo->work_n2);
+      uint32_t ls = warp_append_n(n_back, &geo->work_n3);
 #pragma unroll
       for (int k = 0; k < kScanItems; ++k) {
         if (v[k] >= dense_min) continue;
@@ -456,10 +527,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
         for (uint32_t q = 0; q < m; ++q) {
           const uint32_t cnt = base + (q < rem ? 1u : 0u);
           const uint2 it = make_uint2(c0 + k, (first << 6) | cnt);
-          if (v[k] >= kHeavy)
-            witem[hs++] = it;
-          else
+          if (sparse[k])
             witem[cap - 1 - ls++] = it;
+          else
+            witem[hs++] = it;
           first += cnt;
         }
       }
@@ -503,7 +574,8 @@ static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStr
   PS_LAUNCH(PS_KID_SCAN, s,
             PS_CUDA(launch_pdl(k_scan, grid_blocks(g, 1), kScanThreads, 0, s, L.count, geo, L.start, with_work ? L.work : nullptr,
                                                                L.witem, g->dense_min, g->item_cap, g->scan_state,
-                                                               g->scan_ctr)));
+                                                               g->scan_ctr, with_work ? g->nbr.start : nullptr,
+                                                               g->stencil)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }

@@ -70,14 +70,18 @@ struct Geo {
   int32_t bbox_key[6];  // order-preserving int keys of min xyz, max xyz
   int32_t status;   // device-side ps_status
   uint32_t work_n;     // dense cells in work[] (CTA-staged kernel)
-  uint32_t work_n2;    // warp items in witem[] (warp kernel)
+  uint32_t work_n2;    // warp items from the front of witem[] (warp kernel)
   uint32_t work_next;  // persistent-kernel work counters
   uint32_t work_next2;
-  uint32_t work_n3;    // light warp items (cells with < kHeavy centrals), witem[cap-1] downwards
+  uint32_t work_n3;    // items from the back of witem[] (sparse cells of central lists), witem[cap-1] downwards
+  uint32_t work_next3; // light items taken so far (query kernel: 32 at a time)
 };
 
 // Warp items with at least this many centrals per cell are listed first (largest work first).
 constexpr uint32_t kHeavy = 16;
+// Central lists: cells with fewer than kHeavy centrals and at most this many candidates in
+// their stencil are "sparse" and listed from the back (one thread per central in the query).
+constexpr uint32_t kSparseCand = 64;
 
 // item i of a list whose heavy items grow from the front and light items from the back
 __device__ __forceinline__ uint2 work_item(const uint2* witem, uint32_t cap, uint32_t n_front, uint32_t i) {
@@ -165,6 +169,8 @@ int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
                        ZeroOut z = ZeroOut());
 int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                  ps_bins bins, float* d_h, cudaStream_t s);
+int run_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_sdm_spec spec,
+            uint64_t* d_hist, uint64_t* d_meta, cudaStream_t s);
 int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                   ps_bins bins, const float* d_G, float* d_grad, float* d_grad_s, cudaStream_t s);
 

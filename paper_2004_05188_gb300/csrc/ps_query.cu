@@ -9,13 +9,13 @@
 // Two persistent kernels take work from device counters (the dynamic
 // schedule):
 //
-//   warp kernel  one warp per item = (cell, batch of <= 32 centrals).  The
-//                candidates are read 32 at a time with one coalesced load into
-//                a per-warp shared buffer (the next batch is prefetched into
-//                registers meanwhile); each lane holds one central and walks
-//                the buffer (shared-memory broadcast).  Items with <= 3
-//                centrals let the lanes split the candidates of each central
-//                and merge their top-k lists by shuffles.
+//   warp kernel  heavy items = (cell with >= 16 centrals, batch of <= 32 of
+//                them): the candidates are read 32 at a time with one coalesced
+//                load into a per-warp shared buffer (the next batch is
+//                prefetched into registers meanwhile); each lane holds one
+//                central and walks the buffer (shared-memory broadcast).
+//                Light items (sparser cells) are taken 32 at a time and each of
+//                their centrals gets one thread that walks its own stencil.
 //   CTA kernel   for cells with >= dense_min centrals (an option): one CTA per
 //                cell; the runs are staged into shared memory with bulk
 //                asynchronous copies (cp.async.bulk, completion on an mbarrier)
@@ -173,6 +173,17 @@ struct Hist {
     }
   }
 
+  // one in-range pair counted straight into the global histogram
+  __device__ __forceinline__ void pair_global(const QueryArgs& a, float d2, uint64_t& binned, uint64_t& below) {
+    if (!RDF) return;
+    if (d2 >= E0) {
+      atomicAdd((unsigned long long*)&a.rdf[bin_index(d2, sE, nb, r0f, inv_dr)], 1ull);
+      ++binned;
+    } else {
+      ++below;
+    }
+  }
+
   // the k-th distance D of one central for the q-th requested k
   __device__ __forceinline__ void kth(const QueryArgs& a, uint32_t q, float D, uint32_t idx) {
     if (a.kth) a.kth[(int64_t)q * a.n + idx] = D;
@@ -223,15 +234,24 @@ __device__ __forceinline__ void add_pair_counters(const QueryArgs& a, uint64_t b
   }
 }
 
+// Rows of the stencil, nearest first: (dy, dz) ordered by dy^2 + dz^2 (the first 9 entries are
+// the 3 x 3 rows of the 27-cell stencil).  Walking the central row first lets the k-th distance
+// of every central settle early, so later candidates rarely enter the top-k lists.
+__constant__ signed char c_row_dy[kMaxRuns] = {0, -1, 1, 0, 0, -1, 1, -1, 1, -2, 2, 0, 0,
+                                               -2, 2, -2, 2, -1, 1, -1, 1, -2, 2, -2, 2};
+__constant__ signed char c_row_dz[kMaxRuns] = {0, 0, 0, -1, 1, -1, -1, 1, 1, 0, 0, -2, 2,
+                                               -1, -1, 1, 1, -2, -2, 2, 2, -2, -2, 2, 2};
+
 // cell c -> run r of its stencil: the x-contiguous records of cells (cx-s .. cx+s, cy+dy, cz+dz)
 __device__ __forceinline__ void cell_run(const QueryArgs& a, const Geo& ng, uint32_t c, uint32_t r, uint32_t& src,
                                          uint32_t& len) {
   const int s = a.stencil, w = 2 * s + 1;
   const uint32_t cx = c % ng.dims[0], cy = (c / ng.dims[0]) % ng.dims[1], cz = c / (ng.dims[0] * ng.dims[1]);
-  const int y = (int)cy + (int)(r % w) - s, z = (int)cz + (int)(r / w) - s;
   src = 0;
   len = 0;
-  if ((int)r < w * w && y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2]) {
+  if ((int)r >= w * w) return;
+  const int y = (int)cy + c_row_dy[r], z = (int)cz + c_row_dz[r];
+  if (y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2]) {
     const uint32_t xlo = cx >= (uint32_t)s ? cx - s : 0;
     const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
     const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
@@ -243,15 +263,25 @@ __device__ __forceinline__ void cell_run(const QueryArgs& a, const Geo& ng, uint
 __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(~0u)); }
 
 // ---------------------------------------------------------------------------
-// warp kernel: one warp per (cell, <= 32 centrals) item
+// warp kernel
+//   heavy items (cells with >= kHeavy centrals, batches of 8..32 centrals): one
+//     lane per central, the candidates staged 32 at a time in the warp's shared
+//     buffer and tested two at a time with packed float32 math;
+//   light items (cells with < kHeavy centrals): the warp takes 32 items at a
+//     time and gives each of their centrals a thread of its own that walks its
+//     own stencil (the records of neighbouring centrals' cells hit in L1).
 // ---------------------------------------------------------------------------
+constexpr uint32_t kHalf = 16;                 // candidates per staging half-batch
+constexpr uint32_t kRowLaneCap = 1u << 25;     // per-central increments of the 32-bit warp row, then global
+
 template <int KMAX, bool RDF>
 __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   griddep_wait();
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
-  __shared__ float s_hits[8][32 * 32];  // per warp: the in-range hits of one batch
+  __shared__ float s_hits[8][32 * kHalf];  // per warp: the in-range hits of one half-batch
+  __shared__ float s_kq[8][32 * kHalf];    // per warp: kNN insertion queue, [slot][lane]
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   constexpr int KK = KMAX > 0 ? KMAX : 1;
   Hist<RDF> H;
@@ -259,20 +289,22 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
   const Geo ng = *a.ngeo;
-  const uint32_t n_front = a.cgeo->work_n2, n_items = n_front + a.cgeo->work_n3;
+  const uint32_t n_front = a.cgeo->work_n2, n_light = a.cgeo->work_n3;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   uint64_t my_binned = 0, my_below = 0;
   float4* buf = s_buf[w];
   float* wlist = s_hits[w];
+  float* kq = s_kq[w];
   uint32_t* rsrc = s_rsrc[w];
   uint32_t* rpre = s_rpre[w];
 
+  // ---- items from the front: dense cells ----
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(&a.cgeo->work_next2, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= n_items) break;
-    const uint2 it = work_item(a.witem, a.work_cap, n_front, item);
+    if (item >= n_front) break;
+    const uint2 it = a.witem[item];
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.cstart[c] + first;
     // run table: sources and prefix counts of the candidate runs
@@ -301,12 +333,12 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     };
 
     if (cnt > 3) {
-      // One lane per central.  32 candidates per coalesced load, staged in the warp's
-      // buffer as 16 interleaved pairs (xa xb ya yb za zb wa wb) and tested two at a time
-      // with packed float32 math.  kNN: each lane updates its own top-k inline (the
-      // threshold test rarely passes once the list is full).  RDF: in-range hits are
-      // appended to a warp-wide list (ballot + popc give each hit its slot) and binned
-      // after the batch by all 32 lanes together.
+      // 32 candidates per coalesced load, staged as 16 interleaved pairs (xa xb ya yb za zb wa wb)
+      // and tested two at a time.  In-range hits go to a warp-wide list (ballot + popc give each
+      // hit its slot) binned by all 32 lanes together; kNN candidates below the lane's current
+      // k-th distance go to the lane's column of the insertion queue, drained after each half-batch
+      // (the sorted insertion then runs with most lanes active instead of once per candidate
+      // whenever any lane needs it).
       const bool valid = lane < cnt;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) p = a.crec[c0 + lane];
@@ -329,38 +361,52 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         }
         __syncwarp();
         nxt = fetch(b + 32 + lane, rr);
-        uint32_t nh = 0;  // hits in the warp list (uniform)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t nh = 0;  // hits in the warp list (uniform)
+          uint32_t qn = 0;  // entries in this lane's queue column
+          const float thr = top[KK - 1];
 #pragma unroll 4
-        for (int t = 0; t < 16; ++t) {
-          const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
-          const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
-          float d2a, d2b;
-          dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
-          float wa, wb;
-          f2_unpack(zw.y, wa, wb);
-          const bool ha = d2a < emax && __float_as_uint(wa) != pidx;
-          const bool hb = d2b < emax && __float_as_uint(wb) != pidx;
-          within += (uint32_t)ha + (uint32_t)hb;
+          for (int t = 8 * half; t < 8 * half + 8; ++t) {
+            const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
+            const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
+            float d2a, d2b;
+            dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
+            float wa, wb;
+            f2_unpack(zw.y, wa, wb);
+            const bool ha = d2a < emax && __float_as_uint(wa) != pidx;
+            const bool hb = d2b < emax && __float_as_uint(wb) != pidx;
+            within += (uint32_t)ha + (uint32_t)hb;
+            if (KMAX > 0) {
+              const bool qa = ha && d2a < thr, qb = hb && d2b < thr;
+              if (qa) kq[qn * 32 + lane] = d2a;
+              qn += (uint32_t)qa;
+              if (qb) kq[qn * 32 + lane] = d2b;
+              qn += (uint32_t)qb;
+            }
+            if (RDF) {
+              const uint32_t ba = __ballot_sync(0xffffffffu, ha);
+              if (ha) wlist[nh + __popc(ba & lt)] = d2a;
+              nh += __popc(ba);
+              const uint32_t bb = __ballot_sync(0xffffffffu, hb);
+              if (hb) wlist[nh + __popc(bb & lt)] = d2b;
+              nh += __popc(bb);
+            }
+          }
           if (KMAX > 0) {
-            if (ha && d2a < top[KK - 1]) topk_insert(top, d2a);
-            if (hb && d2b < top[KK - 1]) topk_insert(top, d2b);
+            const uint32_t m = __reduce_max_sync(0xffffffffu, qn);
+            for (uint32_t q = 0; q < m; ++q)
+              if (q < qn) topk_insert(top, kq[q * 32 + lane]);
           }
           if (RDF) {
-            const uint32_t ba = __ballot_sync(0xffffffffu, ha);
-            if (ha) wlist[nh + __popc(ba & lt)] = d2a;
-            nh += __popc(ba);
-            const uint32_t bb = __ballot_sync(0xffffffffu, hb);
-            if (hb) wlist[nh + __popc(bb & lt)] = d2b;
-            nh += __popc(bb);
-          }
-        }
-        if (RDF) {
-          __syncwarp();
-          for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], my_binned, my_below);
-          wcount += nh;
-          if (wcount >= (1ull << 31)) {
-            H.flush_warp(a);
-            wcount = 0;
+            __syncwarp();
+            for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], my_binned, my_below);
+            __syncwarp();
+            wcount += nh;
+            if (wcount >= (1ull << 31)) {
+              H.flush_warp(a);
+              wcount = 0;
+            }
           }
         }
       }
@@ -370,7 +416,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
       }
     } else {
-      // few centrals: the lanes split the candidates of each central
+      // few centrals, many candidates: the lanes split the candidates of each central and
+      // merge their sorted lists by shuffles
       for (uint32_t ci = 0; ci < cnt; ++ci) {
         const float4 p = a.crec[c0 + ci];
         const uint32_t pidx = __float_as_uint(p.w);
@@ -415,6 +462,88 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         }
       }
     }
+  }
+
+  // ---- items from the back: sparse cells, one thread per central ----
+  // central record and cell of the taken items' centrals (<= 32 * 15, kHeavy - 1 per item)
+  uint32_t* cl_rec = reinterpret_cast<uint32_t*>(s_hits[w]);
+  uint32_t* cl_cell = reinterpret_cast<uint32_t*>(s_kq[w]);
+  const int st = a.stencil;
+  // items per take: enough that every warp of the grid gets work when the list is short
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t take = min(32u, max(1u, (n_light + n_warps - 1) / n_warps));
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.cgeo->work_next3, take);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_light) break;
+    uint32_t c = 0, f = 0, cnt = 0;
+    if (lane < take && base + lane < n_light) {
+      const uint2 it = a.witem[a.work_cap - 1 - (base + lane)];
+      c = it.x;
+      f = a.cstart[c] + (it.y >> 6);
+      cnt = it.y & 63u;
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    __syncwarp();
+    for (uint32_t q = 0; q < cnt; ++q) cl_rec[inc - cnt + q] = f + q, cl_cell[inc - cnt + q] = c;
+    __syncwarp();
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+      const bool valid = r0 + lane < total;
+      uint32_t rowc = 0;  // increments of the warp row by this lane
+      if (valid) {
+        const uint32_t ce = cl_cell[r0 + lane];
+        const float4 p = __ldg(a.crec + cl_rec[r0 + lane]);
+        const uint32_t pidx = __float_as_uint(p.w);
+        const uint32_t cx = ce % ng.dims[0], cy = (ce / ng.dims[0]) % ng.dims[1], cz = ce / (ng.dims[0] * ng.dims[1]);
+        const uint32_t xlo = cx >= (uint32_t)st ? cx - st : 0;
+        const uint32_t xhi = cx + st < ng.dims[0] ? cx + st : ng.dims[0] - 1;
+        const int ylo = max((int)cy - st, 0), yhi = min((int)cy + st, (int)ng.dims[1] - 1);
+        const int zlo = max((int)cz - st, 0), zhi = min((int)cz + st, (int)ng.dims[2] - 1);
+        float top[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) top[t] = INFINITY;
+        uint32_t within = 0;
+        for (int z = zlo; z <= zhi; ++z)
+          for (int y = ylo; y <= yhi; ++y) {
+            const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+            const uint32_t j1 = a.nstart[row + xhi + 1];
+            for (uint32_t j = a.nstart[row + xlo]; j < j1; ++j) {
+              const float4 q = __ldg(a.nrec + j);
+              const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+              if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
+                ++within;
+                if (RDF) {
+                  if (within <= kRowLaneCap)
+                    H.pair(a, d2, my_binned, my_below);
+                  else
+                    H.pair_global(a, d2, my_binned, my_below);
+                }
+                if (KMAX > 0 && d2 < top[KK - 1]) topk_insert(top, d2);
+              }
+            }
+          }
+        rowc = within < kRowLaneCap ? within : kRowLaneCap;
+        if (a.nwithin) a.nwithin[pidx] = within;
+        if (KMAX > 0)
+          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
+      }
+      if (RDF) {
+        // a round adds at most 32 * 2^25 = 2^30 to the row: flushed at 2^31, it never wraps
+        wcount += __reduce_add_sync(0xffffffffu, rowc);
+        if (wcount >= (1ull << 31)) {
+          H.flush_warp(a);
+          wcount = 0;
+        }
+      }
+    }
+    __syncwarp();  // cl is rewritten next
   }
   H.flush(a);
   add_pair_counters(a, my_binned, my_below);
@@ -571,6 +700,7 @@ static int dispatch_k(const ps_grid* g, const QueryArgs& qa, uint32_t sc, uint32
   if (k <= 2) return launch_query<2, RDF>(g, qa, sc, sw, s);
   if (k <= 4) return launch_query<4, RDF>(g, qa, sc, sw, s);
   if (k <= 8) return launch_query<8, RDF>(g, qa, sc, sw, s);
+  if (k <= 12) return launch_query<12, RDF>(g, qa, sc, sw, s);
   if (k <= 16) return launch_query<16, RDF>(g, qa, sc, sw, s);
   return launch_query<32, RDF>(g, qa, sc, sw, s);
 }
