@@ -12,7 +12,9 @@ the d_srf edge rule (Methods, "Ion-to-edge distancing") and per-ROI
 enumeration (Suppl., "Customized user defined batch processing queues").
 The spatial distribution map (the 3-D two-point statistic, same Methods
 passage; voxelised displacements within the ROI radius R, Results on strong
-scaling) bins the float32 displacement of every in-range pair.
+scaling) bins the float32 displacement of every in-range pair.  Maximum-separation
+clustering (same Methods passage: DBScan with d_max and N_min) labels the
+connected components of the d_max graph.
 The smoothed-RDF functions are FP64.  Parity for the g(r) normalisation
 constants is unpinned (the paper gives no formula); everything else is
 pinned by the tests under tests/test_oracle_*.py.
@@ -68,6 +70,8 @@ def _load():
         lib.orc_sdm_edges.restype = None
         lib.orc_sdm.argtypes = [P, P, P, i64, P, P, f32, f64, f64, u32, P, P]
         lib.orc_sdm.restype = ctypes.c_int
+        lib.orc_cluster.argtypes = [P, P, P, i64, P, f64, u32, f32, u32, P, P, P, P]
+        lib.orc_cluster.restype = ctypes.c_int
         lib.orc_label_perm.argtypes = [i64, ctypes.c_uint64, P]
         lib.orc_label_perm.restype = None
         lib.orc_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64]
@@ -195,6 +199,22 @@ def sdm(xyz, type_, dsrf, ctr_types, nbr_types, dsrf_min, r_max, w, n_vox):
     if rc != 0:
         raise RuntimeError(f"oracle sdm failed: {rc}")
     return H, meta
+
+
+def cluster(xyz, type_, dsrf, types, d_max, n_min, dsrf_min=0.0, hist_len=1024):
+    """Maximum-separation clustering (see oracle.c).  Returns dict(label uint32 [n], size_hist,
+    interior_hist uint64 [hist_len], n_set, n_clusters, n_clustered, n_interior)."""
+    xyz, type_, dsrf, n = _prep(xyz, type_, dsrf)
+    label = np.empty(n, np.uint32)
+    sh = np.zeros(hist_len, np.uint64)
+    ih = np.zeros(hist_len, np.uint64)
+    meta = np.zeros(4, np.uint64)
+    rc = _load().orc_cluster(_ptr(xyz), _ptr(type_), _ptr(dsrf), n, _ptr(type_mask(types)), float(d_max), int(n_min),
+                             float(dsrf_min), int(hist_len), _ptr(label), _ptr(sh), _ptr(ih), _ptr(meta))
+    if rc != 0:
+        raise RuntimeError(f"oracle cluster failed: {rc}")
+    return dict(label=label, size_hist=sh, interior_hist=ih, n_set=int(meta[0]), n_clusters=int(meta[1]),
+                n_clustered=int(meta[2]), n_interior=int(meta[3]))
 
 
 def label_perm(n: int, seed: int) -> np.ndarray:

@@ -32,7 +32,10 @@
  *     Gaussian), over the pairs with s*d < stop + 6 sigma;
  *   - spatial distribution map: the pairs with d2 < (float)(R*R) binned by
  *     their float32 displacement x_j - x_i into cubic voxels, edges
- *     V[m] = (float)((m - n_vox/2) * w), half-open on every axis.
+ *     V[m] = (float)((m - n_vox/2) * w), half-open on every axis;
+ *   - maximum-separation clustering: ions linked when d2 <= (float)(d_max^2)
+ *     (closed, as the eps-neighbourhood of DBScan), clusters = connected
+ *     components with >= N_min ions, labelled by their smallest ion index.
  *
  * Status codes: 0 ok, 1 bad argument, 2 out of memory.
  */
@@ -427,6 +430,149 @@ done:
   free(item);
   free(start);
   free(V);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Maximum-separation clustering (Methods, "Descriptive, two-point spatial    */
+/* statistics, and clustering": the DBScan variant with the threshold          */
+/* distance d_max and the minimum cluster size N_min; Results on the AM        */
+/* specimens for the post-processing of the labels).                          */
+/*                                                                            */
+/*  Ions of the chosen types are linked when d2 <= (float)(d_max^2) (float32  */
+/*  d2 as everywhere); clusters are the connected components with at least    */
+/*  n_min ions.  Outputs:                                                     */
+/*   label[n]  smallest original index in the ion's cluster, or 0xFFFFFFFF     */
+/*             (other types, or a component smaller than n_min)               */
+/*   size_hist[hist_len]  clusters by size (sizes >= hist_len-1 in the last    */
+/*             entry); interior_hist likewise for the clusters whose members  */
+/*             all have d_srf >= dsrf_min (not truncated by the edge)         */
+/*   meta = {n_set, n_clusters, ions in clusters, interior clusters}          */
+/* ------------------------------------------------------------------------- */
+static int64_t uf_find(int64_t* parent, int64_t x) {
+  while (parent[x] != x) x = parent[x];
+  return x;
+}
+
+int orc_cluster(const float* xyz, const uint8_t* type, const float* dsrf, int64_t n, const uint64_t* mask,
+                double d_max, uint32_t n_min, float dsrf_min, uint32_t hist_len, uint32_t* label,
+                uint64_t* size_hist, uint64_t* interior_hist, uint64_t* meta) {
+  if (n < 0 || !(d_max > 0) || n_min < 1 || hist_len < 2) return ORC_ERR_ARG;
+  const float D = (float)(d_max * d_max);
+  memset(size_hist, 0, (size_t)hist_len * sizeof(uint64_t));
+  memset(interior_hist, 0, (size_t)hist_len * sizeof(uint64_t));
+  meta[0] = meta[1] = meta[2] = meta[3] = 0;
+  for (int64_t i = 0; i < n; ++i) label[i] = 0xFFFFFFFFu;
+  int64_t* parent = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  int64_t* csize = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int64_t* cmin = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  float* cdmin = (float*)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+  int64_t* start = NULL;
+  int64_t* item = NULL;
+  int64_t* fill = NULL;
+  int rc = ORC_OK;
+  if (!parent || !csize || !cmin || !cdmin) {
+    rc = ORC_ERR_OOM;
+    goto done;
+  }
+  for (int64_t i = 0; i < n; ++i) parent[i] = i;
+  /* cell list of the set, cells of edge just above d_max */
+  {
+    const double h = sqrt((double)D) * (1.0 + 1e-5) + 1e-6;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int64_t nn = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (!in_mask(mask, type[j])) continue;
+      ++nn;
+      for (int a = 0; a < 3; ++a) {
+        if (xyz[3 * j + a] < lo[a]) lo[a] = xyz[3 * j + a];
+        if (xyz[3 * j + a] > hi[a]) hi[a] = xyz[3 * j + a];
+      }
+    }
+    meta[0] = (uint64_t)nn;
+    int64_t dim[3] = {1, 1, 1};
+    if (nn > 0)
+      for (int a = 0; a < 3; ++a) dim[a] = (int64_t)floor((hi[a] - lo[a]) / h) + 1;
+    else
+      lo[0] = lo[1] = lo[2] = 0.0;
+    const int64_t ncell = dim[0] * dim[1] * dim[2];
+    start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    item = (int64_t*)malloc((size_t)(nn > 0 ? nn : 1) * sizeof(int64_t));
+    fill = (int64_t*)calloc((size_t)ncell, sizeof(int64_t));
+    if (!start || !item || !fill) {
+      rc = ORC_ERR_OOM;
+      goto done;
+    }
+#define CELLK(x, a) ((int64_t)fmin(fmax(floor(((double)(x) - lo[a]) / h), 0.0), (double)(dim[a] - 1)))
+    for (int64_t j = 0; j < n; ++j) {
+      if (!in_mask(mask, type[j])) continue;
+      start[(CELLK(xyz[3 * j + 2], 2) * dim[1] + CELLK(xyz[3 * j + 1], 1)) * dim[0] + CELLK(xyz[3 * j], 0) + 1] += 1;
+    }
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    for (int64_t j = 0; j < n; ++j) {
+      if (!in_mask(mask, type[j])) continue;
+      const int64_t c = (CELLK(xyz[3 * j + 2], 2) * dim[1] + CELLK(xyz[3 * j + 1], 1)) * dim[0] + CELLK(xyz[3 * j], 0);
+      item[start[c] + fill[c]++] = j;
+    }
+    /* link every pair within d_max: union of the two components (larger root under the smaller) */
+    for (int64_t i = 0; i < n; ++i) {
+      if (!in_mask(mask, type[i])) continue;
+      const float* xi = xyz + 3 * i;
+      const int64_t cx = CELLK(xi[0], 0), cy = CELLK(xi[1], 1), cz = CELLK(xi[2], 2);
+      for (int64_t z = cz - 1; z <= cz + 1; ++z)
+        for (int64_t y = cy - 1; y <= cy + 1; ++y)
+          for (int64_t x = cx - 1; x <= cx + 1; ++x) {
+            if (x < 0 || y < 0 || z < 0 || x >= dim[0] || y >= dim[1] || z >= dim[2]) continue;
+            const int64_t c = (z * dim[1] + y) * dim[0] + x;
+            for (int64_t t = start[c]; t < start[c + 1]; ++t) {
+              const int64_t j = item[t];
+              if (j <= i || !(dist2(xi, xyz + 3 * j) <= D)) continue;
+              const int64_t ri = uf_find(parent, i), rj = uf_find(parent, j);
+              if (ri < rj)
+                parent[rj] = ri;
+              else if (rj < ri)
+                parent[ri] = rj;
+            }
+          }
+    }
+#undef CELLK
+  }
+  /* components: the root is the smallest index of the component */
+  for (int64_t i = 0; i < n; ++i) {
+    cmin[i] = -1;
+    cdmin[i] = INFINITY;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (!in_mask(mask, type[i])) continue;
+    const int64_t r = uf_find(parent, i);
+    csize[r] += 1;
+    if (cmin[r] < 0 || i < cmin[r]) cmin[r] = i;
+    if (dsrf[i] < cdmin[r]) cdmin[r] = dsrf[i];
+  }
+  for (int64_t r = 0; r < n; ++r) {
+    if (csize[r] < (int64_t)n_min) continue;
+    const uint32_t b = csize[r] >= (int64_t)hist_len - 1 ? hist_len - 1 : (uint32_t)csize[r];
+    size_hist[b] += 1;
+    meta[1] += 1;
+    meta[2] += (uint64_t)csize[r];
+    if (cdmin[r] >= dsrf_min) {
+      interior_hist[b] += 1;
+      meta[3] += 1;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (!in_mask(mask, type[i])) continue;
+    const int64_t r = uf_find(parent, i);
+    if (csize[r] >= (int64_t)n_min) label[i] = (uint32_t)cmin[r];
+  }
+done:
+  free(fill);
+  free(item);
+  free(start);
+  free(cdmin);
+  free(cmin);
+  free(csize);
+  free(parent);
   return rc;
 }
 
