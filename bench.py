@@ -427,6 +427,52 @@ def measure_sdm(args, dev):
     return res
 
 
+def measure_cluster(args, dev):
+    """Maximum-separation clustering of the Sc ions of the 8.07e6-ion needle over the paper's
+    synthetic-benchmark sweep d_max = [0.10, 0.05, 0.70] nm (13 runs), N_min = 5; clusters whose
+    ions all have d_srf >= 2 nm count as interior.  Each run = grid build + clustering."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+
+    xyz, t, d = make_cloud("needle8m")
+    N = xyz.shape[0]
+    X = torch.from_numpy(xyz).to(dev)
+    T = torch.from_numpy(t).to(dev)
+    D = torch.from_numpy(d).to(dev)
+    d_maxes = [round(0.10 + 0.05 * i, 2) for i in range(13)]
+    g = ps.Grid(N)
+    out = None
+
+    def run(dm):
+        nonlocal out
+        g.build(X, T, [1], dm * (1 + 1e-6))  # r_cut just above d_max: float32 r_cut^2 >= (float)(d_max^2)
+        out = ps.cluster(g, D, dm, 5, 2.0, 1024, out=out)
+
+    run(d_maxes[-1])
+    torch.cuda.synchronize()
+    rows = []
+    total = 0.0
+    for dm in d_maxes:
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run(dm)
+            e1.record()
+            torch.cuda.synchronize()
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+        m = out["meta"].cpu().numpy()
+        if m[4] != 0:
+            raise RuntimeError(f"clustering status {m[4]}")
+        rows.append({"d_max": dm, "ms": round(best, 4), "clusters": int(m[1]), "ions_in_clusters": int(m[2]),
+                     "interior_clusters": int(m[3])})
+        total += best
+    g.close()
+    return {"workload": f"needle {N} ions, Sc ({int(m[0])} ions), d_max=[0.10,0.05,0.70] nm, N_min=5",
+            "sweep_ms": total, "runs": rows, "timing": "CUDA events, eager, grid build included, best of 3 per run"}
+
+
 def measure_batched(args, dev):
     """256 ROIs (needles and cylinders, log-uniform 1e4..1e7 ions), each with the sweep
     k = 1..20, r_max in {1, 2, 3} nm (0.01 nm bins), d_srf >= {0, 1, 2} nm, type pairs
@@ -742,6 +788,7 @@ def run_gpu(args, wl_name, wl):
         if args.batch_rois > 0:
             forms["batched"] = measure_batched(args, dev)
         forms["sdm"] = measure_sdm(args, dev)
+        forms["cluster"] = measure_cluster(args, dev)
 
     # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
@@ -798,7 +845,7 @@ def main():
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
     ap.add_argument("--no-autotune", action="store_true", help="use --cell-scale/--dense-min instead of the autotuner")
-    ap.add_argument("--only-form", choices=["soft", "batched", "sdm"],
+    ap.add_argument("--only-form", choices=["soft", "batched", "sdm", "cluster"],
                     help="measure only this form (no exact step line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -815,7 +862,8 @@ def main():
 
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
-        fn = {"soft": measure_soft, "batched": measure_batched, "sdm": measure_sdm}[args.only_form]
+        fn = {"soft": measure_soft, "batched": measure_batched, "sdm": measure_sdm,
+              "cluster": measure_cluster}[args.only_form]
         print(json.dumps({"form": args.only_form, **fn(args, dev)}), flush=True)
         return 0
     return run_gpu(args, args.workload, wl)

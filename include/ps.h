@@ -287,6 +287,36 @@ PS_API int ps_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
                   uint64_t* d_hist, uint64_t* d_meta, void* stream);
 
 /*
+ * Maximum-separation clustering (Methods, "Descriptive, two-point spatial
+ * statistics, and clustering": the DBScan variant with threshold distance
+ * d_max and minimum cluster size N_min; Results on the AM specimens for the
+ * d_max sweeps and the clusters truncated by the dataset edge).
+ *   The ions of the grid's set (its neighbour types) are linked when
+ *   d2 <= (float)(d_max^2) (float32 d2 as in ps_spatstat); clusters are the
+ *   connected components with at least n_min ions.
+ *   g        grid built with r_cut >= d_max (else PS_ERR_INVALID_ARG); its
+ *            central-list storage is used as scratch (later queries rebuild it)
+ *   dsrf     device float32 [n] or NULL: a cluster is "interior" when all its
+ *            ions have d_srf >= spec.dsrf_min (NULL: every cluster)
+ *   d_label  device uint32 [n]: the smallest original index of the ion's
+ *            cluster, or 0xFFFFFFFF (other types, or a component below n_min)
+ *   d_size_hist, d_interior_hist  device uint64 [hist_len]: clusters by size
+ *            (sizes >= hist_len - 1 in the last entry), all / interior only
+ *   d_meta   device uint64 [PS_CLUSTER_META_LEN]: ions in the set, clusters,
+ *            ions in clusters, interior clusters, status
+ * All outputs are overwritten.  Asynchronous on `stream`.  n < 2^32 - 1.
+ */
+#define PS_CLUSTER_META_LEN 5
+typedef struct {
+  double d_max;     /* link distance (nm) */
+  uint32_t n_min;   /* smallest cluster, >= 1 */
+  float dsrf_min;   /* interior threshold on d_srf */
+  uint32_t hist_len; /* >= 2 */
+} ps_cluster_spec;
+PS_API int ps_cluster(ps_grid* g, const float* dsrf, ps_cluster_spec spec, uint32_t* d_label, uint64_t* d_size_hist,
+                      uint64_t* d_interior_hist, uint64_t* d_meta, void* stream);
+
+/*
  * Randomised type labels: the paper computes every statistic also for a
  * random relabelling of the ions, as the reference for a random arrangement
  * (Suppl. "Importance of high quality random number generators").
@@ -355,7 +385,8 @@ typedef enum {
   PS_KID_BATCH = 12,     /* batched sweep kernels */
   PS_KID_LABELS = 13,    /* randomised labels */
   PS_KID_SDM = 14,       /* spatial distribution map */
-  PS_KID_COUNT_ = 15
+  PS_KID_CLUSTER = 15,   /* maximum-separation clustering */
+  PS_KID_COUNT_ = 16
 } ps_kernel_id;
 PS_API uint64_t ps_launch_count(void);
 PS_API int ps_prof_enable(uint32_t kid_mask);

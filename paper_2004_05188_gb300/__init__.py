@@ -85,6 +85,11 @@ class SdmSpec(ctypes.Structure):
     _fields_ = [("r_max", ctypes.c_double), ("w", ctypes.c_double), ("n_vox", ctypes.c_uint32)]
 
 
+class ClusterSpec(ctypes.Structure):
+    _fields_ = [("d_max", ctypes.c_double), ("n_min", ctypes.c_uint32), ("dsrf_min", ctypes.c_float),
+                ("hist_len", ctypes.c_uint32)]
+
+
 class Sweep(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("bins", Bins), ("n_rmax", ctypes.c_uint32),
                 ("rmax_bins", ctypes.c_uint32 * 4), ("n_dsrf", ctypes.c_uint32), ("dsrf_min", ctypes.c_float * 4),
@@ -131,6 +136,7 @@ def lib():
     L.ps_rdf_soft_bwd.argtypes = [P, P, P, f32, f32, f32, Bins, P, P, P, P]
     L.ps_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64, P, P]
     L.ps_sdm.argtypes = [P, P, P, f32, SdmSpec, P, P, P]
+    L.ps_cluster.argtypes = [P, P, ClusterSpec, P, P, P, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
@@ -145,7 +151,7 @@ def _check(rc: int):
 
 
 KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
-           soft_bwd=11, batch=12, labels=13, sdm=14)
+           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15)
 
 
 def launch_count() -> int:
@@ -335,6 +341,30 @@ def sdm(grid: Grid, dsrf, ctr_types, dsrf_min: float, r_max: float, w: float, n_
     m, mp = _mask_ptr(ctr_types)
     _check(lib().ps_sdm(grid.handle, _ptr(dsrf), mp, float(dsrf_min), SdmSpec(float(r_max), float(w), int(n_vox)),
                         _ptr(out["H"]), _ptr(out["meta"]), _stream(stream)))
+    return out
+
+
+CLUSTER_META_LEN = 5
+
+
+def cluster(grid: Grid, dsrf, d_max: float, n_min: int, dsrf_min: float = 0.0, hist_len: int = 1024, out=None,
+            stream=None):
+    """Maximum-separation clustering of the grid's set (ps_cluster).  Returns {"label": int32 [n]
+    (smallest original index of the ion's cluster, -1 if none), "size_hist", "interior_hist":
+    int64 [hist_len], "meta": int64 [5] = ions in the set, clusters, ions in clusters, interior
+    clusters, status}."""
+    import torch
+
+    dev = grid._refs[0].device
+    n = grid._refs[0].shape[0]
+    if out is None:
+        out = dict(label=torch.empty(n, dtype=torch.int32, device=dev),
+                   size_hist=torch.empty(hist_len, dtype=torch.int64, device=dev),
+                   interior_hist=torch.empty(hist_len, dtype=torch.int64, device=dev),
+                   meta=torch.empty(CLUSTER_META_LEN, dtype=torch.int64, device=dev))
+    spec = ClusterSpec(float(d_max), int(n_min), float(dsrf_min), int(hist_len))
+    _check(lib().ps_cluster(grid.handle, _ptr(dsrf), spec, _ptr(out["label"]), _ptr(out["size_hist"]),
+                            _ptr(out["interior_hist"]), _ptr(out["meta"]), _stream(stream)))
     return out
 
 

@@ -102,7 +102,7 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   const size_t o_sel = take(nm * 4), o_cr = take(nm * 8);
   const size_t o_ncount = take(cc * 4), o_nstart = take((cc + 1) * 4), o_nrec = take(nm * 16);
   const size_t o_ccount = take(cc * 4), o_cstart = take((cc + 1) * 4), o_crec = take(nm * 16), o_cwork = take(cc * 4);
-  g->item_cap = (uint32_t)(cc + nm / 32 + 2);
+  g->item_cap = (uint32_t)(cc + nm / 8 + 2);  // batches of >= 8 centrals (4 lanes per central) + one per cell
   const size_t o_witem = take((size_t)g->item_cap * 8), o_nwitem = take((size_t)g->item_cap * 8);
   const size_t o_sm0 = take(kSoftFineMax * 8), o_sm1 = take(kSoftFineMax * 8), o_sm2 = take(kSoftFineMax * 8);
   const size_t o_sT = take(3 * kSoftFineMax * 4), o_sgs = take(8);
@@ -249,6 +249,21 @@ int ps_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf
   if ((double)ER > (double)g->r_cut * (double)g->r_cut)
     return fail(PS_ERR_INVALID_ARG, "ps_sdm: the grid's r_cut is below r_max");
   return run_sdm(g, dsrf, ctr_mask, dsrf_min, spec, d_hist, d_meta, static_cast<cudaStream_t>(stream));
+}
+
+int ps_cluster(ps_grid* g, const float* dsrf, ps_cluster_spec spec, uint32_t* d_label, uint64_t* d_size_hist,
+               uint64_t* d_interior_hist, uint64_t* d_meta, void* stream) {
+  if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "ps_cluster: grid is NULL or not built");
+  if (!d_label || !d_size_hist || !d_interior_hist || !d_meta)
+    return fail(PS_ERR_INVALID_ARG, "ps_cluster: an output pointer is NULL");
+  if (!(spec.d_max > 0.0) || !std::isfinite(spec.d_max)) return fail(PS_ERR_INVALID_ARG, "ps_cluster: d_max must be > 0");
+  if (spec.n_min < 1 || spec.hist_len < 2) return fail(PS_ERR_INVALID_ARG, "ps_cluster: n_min >= 1 and hist_len >= 2");
+  if (std::isnan(spec.dsrf_min)) return fail(PS_ERR_INVALID_ARG, "ps_cluster: dsrf_min is NaN");
+  if (g->n >= (int64_t)0xFFFFFFFF) return fail(PS_ERR_UNSUPPORTED, "ps_cluster: n must be below 2^32 - 1");
+  const float D = (float)(spec.d_max * spec.d_max);
+  if ((double)D > (double)g->r_cut * (double)g->r_cut)
+    return fail(PS_ERR_INVALID_ARG, "ps_cluster: the grid's r_cut is below d_max");
+  return run_cluster(g, dsrf, spec, d_label, d_size_hist, d_interior_hist, d_meta, static_cast<cudaStream_t>(stream));
 }
 
 static int check_soft(ps_grid* g, const uint64_t* ctr_mask, ps_bins bins, float dsrf_min) {

@@ -384,18 +384,22 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return prefix + x - v;
 }
 
-// Candidates of cell c: the neighbour records in the cells within `st` cells of it.
+// Candidates of cell c: the neighbour records in the cells within `st` (1 or 2) cells of it.
+// The row loops are unrolled over the largest stencil so that the loads issue together.
 __device__ __forceinline__ uint32_t stencil_count(const uint32_t* __restrict__ nstart, const Geo* g, uint32_t c, int st) {
   const uint32_t d0 = g->dims[0], d1 = g->dims[1], d2 = g->dims[2];
   const uint32_t cx = c % d0, cy = (c / d0) % d1, cz = c / (d0 * d1);
   const uint32_t xlo = cx >= (uint32_t)st ? cx - st : 0, xhi = cx + st < d0 ? cx + st : d0 - 1;
-  const int ylo = max((int)cy - st, 0), yhi = min((int)cy + st, (int)d1 - 1);
-  const int zlo = max((int)cz - st, 0), zhi = min((int)cz + st, (int)d2 - 1);
   uint32_t n = 0;
-  for (int z = zlo; z <= zhi; ++z)
-    for (int y = ylo; y <= yhi; ++y) {
-      const uint32_t row = ((uint32_t)z * d1 + (uint32_t)y) * d0;
-      n += nstart[row + xhi + 1] - nstart[row + xlo];
+#pragma unroll
+  for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+    for (int dy = -2; dy <= 2; ++dy) {
+      const int z = (int)cz + dz, y = (int)cy + dy;
+      if (dz >= -st && dz <= st && dy >= -st && dy <= st && z >= 0 && y >= 0 && z < (int)d2 && y < (int)d1) {
+        const uint32_t row = ((uint32_t)z * d1 + (uint32_t)y) * d0;
+        n += __ldg(nstart + row + xhi + 1) - __ldg(nstart + row + xlo);
+      }
     }
   return n;
 }
@@ -403,7 +407,11 @@ __device__ __forceinline__ uint32_t stencil_count(const uint32_t* __restrict__ n
 // Warp items of a cell with n centrals: n <= 3 gives one item (the lanes of
 // the warp split the candidates of each central); otherwise ceil(n/32)
 // balanced batches of at most 32 centrals (one lane per central).
-__device__ __forceinline__ uint32_t items_of(uint32_t n) { return n == 0 ? 0u : (n <= 3 ? 1u : (n + 31u) / 32u); }
+// With L lanes per central an item holds at most 32 / L centrals.
+__device__ __forceinline__ uint32_t items_of(uint32_t n, uint32_t L = 1) {
+  const uint32_t per = 32u / L;
+  return n == 0 ? 0u : (n <= 3 ? 1u : (n + per - 1u) / per);
+}
 
 // look-back words: flag in bits 62-63 (1: tile aggregate, 2: inclusive prefix), value in bits 0-31
 constexpr unsigned long long kFlagA = 1ull << 62, kFlagP = 2ull << 62;
@@ -426,12 +434,13 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 // `work` (CTA kernel), the others are split into warp items (cell,
 // first << 6 | count): sparse cells (fewer than kHeavy centrals and at most
 // kSparseCand candidates in the stencil of the neighbour grid `nstart`) from
-// the back of `witem`, the rest from the front.
+// the back of `witem`, the rest from the front, in batches of at most
+// 32 / lanes_per_central centrals when `split` is set.
 __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ count, Geo* geo,
                                                        uint32_t* __restrict__ start, uint32_t* __restrict__ work,
                                                        uint2* __restrict__ witem, uint32_t dense_min, uint32_t cap,
                                                        unsigned long long* state, uint32_t* ctr,
-                                                       const uint32_t* __restrict__ nstart, int stencil) {
+                                                       const uint32_t* __restrict__ nstart, int stencil, bool split) {
   griddep_wait();
   griddep_launch();
   __shared__ uint32_t s_warp[32];
@@ -506,21 +515,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
     if (work != nullptr) {
       uint32_t n_front = 0, n_back = 0;
       bool sparse[kScanItems];
+      uint32_t lanes[kScanItems];
+      const uint32_t n_nbr = nstart != nullptr ? nstart[nc] : 0u;
 #pragma unroll
       for (int k = 0; k < kScanItems; ++k) {
         const bool dense = (c0 + k < nc) && v[k] >= dense_min;
         const uint32_t s1 = warp_append(dense, &geo->work_n);
         if (dense) work[s1] = c0 + k;
-        sparse[k] = !dense && v[k] > 0 && v[k] < kHeavy && nstart != nullptr &&
-                    stencil_count(nstart, geo, c0 + k, stencil) <= kSparseCand;
-        if (!dense) (sparse[k] ? n_back : n_front) += items_of(v[k]);
+        const uint32_t cand = (!dense && v[k] > 0 && nstart != nullptr) ? stencil_count(nstart, geo, c0 + k, stencil) : 0u;
+        sparse[k] = !dense && v[k] > 0 && v[k] < kHeavy && nstart != nullptr && cand <= kSparseCand;
+        lanes[k] = (split && !sparse[k] && v[k] > 3) ? lanes_per_central(cand, n_nbr, nc, stencil) : 1u;
+        if (!dense) (sparse[k] ? n_back : n_front) += items_of(v[k], lanes[k]);
       }
       uint32_t hs = warp_append_n(n_front, &geo->work_n2);
       uint32_t ls = warp_append_n(n_back, &geo->work_n3);
 #pragma unroll
       for (int k = 0; k < kScanItems; ++k) {
         if (v[k] >= dense_min) continue;
-        const uint32_t m = items_of(v[k]);
+        const uint32_t m = items_of(v[k], lanes[k]);
         if (m == 0) continue;
         const uint32_t base = v[k] / m, rem = v[k] % m;
         uint32_t first = 0;
@@ -570,12 +582,12 @@ static int grid_blocks(const ps_grid* g, int per_sm) { return g->num_sms * per_s
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStream_t s) {
+static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStream_t s, bool split = false) {
   PS_LAUNCH(PS_KID_SCAN, s,
             PS_CUDA(launch_pdl(k_scan, grid_blocks(g, 1), kScanThreads, 0, s, L.count, geo, L.start, with_work ? L.work : nullptr,
                                                                L.witem, g->dense_min, g->item_cap, g->scan_state,
                                                                g->scan_ctr, with_work ? g->nbr.start : nullptr,
-                                                               g->stencil)));
+                                                               g->stencil, split)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -602,7 +614,7 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
 }
 
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
-                       ZeroOut z) {
+                       ZeroOut z, bool split) {
   Mask m;
   for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w];
   const bool vec = aligned16(g->type) && aligned16(g->xyz) && (dsrf == nullptr || aligned16(dsrf));
@@ -613,7 +625,7 @@ int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
               PS_CUDA(launch_pdl(k_central_select_count, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->type, dsrf, g->n, m, dsrf_min,
                                                                               vec, g->nbr.geo, g->ctr.geo, g->ctr.count,
                                                                               g->sel, g->cr)));
-  int rc = scan_cells(g, g->ctr, g->ctr.geo, true, s);
+  int rc = scan_cells(g, g->ctr, g->ctr.geo, true, s, split);
   if (rc) return rc;
   PS_LAUNCH(PS_KID_SCATTER, s,
             PS_CUDA(launch_pdl(k_scatter, grid_blocks(g, 8), kThreads, 0, s, g->xyz, g->sel, g->cr, g->ctr.start, g->ctr.geo, g->ctr.rec,

@@ -83,6 +83,19 @@ constexpr uint32_t kHeavy = 16;
 // their stencil are "sparse" and listed from the back (one thread per central in the query).
 constexpr uint32_t kSparseCand = 64;
 
+// Lanes that share one central's candidates in the query's staged path: 1, or 2 / 4 for cells
+// whose stencil holds at least 32 / 64 times the cloud's mean number of candidates (n_nbr
+// records over n_cells cells, (2s+1)^3 cells per stencil), so that the items of extreme
+// clusters do not set the kernel's length on their own (on a saturated GPU the split costs
+// more instructions than it saves).  Integer arithmetic: the central-list scan and the query
+// compute the same value.
+__host__ __device__ __forceinline__ uint32_t lanes_per_central(uint32_t n_cand, uint32_t n_nbr, uint32_t n_cells,
+                                                               int stencil) {
+  const uint64_t w = (uint64_t)(2 * stencil + 1) * (2 * stencil + 1) * (2 * stencil + 1);
+  const uint64_t lhs = (uint64_t)n_cand * n_cells, unit = w * n_nbr;
+  return lhs >= 64 * unit ? 4u : (lhs >= 32 * unit ? 2u : 1u);
+}
+
 // item i of a list whose heavy items grow from the front and light items from the back
 __device__ __forceinline__ uint2 work_item(const uint2* witem, uint32_t cap, uint32_t n_front, uint32_t i) {
   return i < n_front ? witem[i] : witem[cap - 1 - (i - n_front)];
@@ -165,12 +178,15 @@ struct ZeroOut {
   uint64_t* p[3] = {nullptr, nullptr, nullptr};
   uint32_t n[3] = {0, 0, 0};
 };
+// split: size the warp items of dense cells for lanes_per_central (the exact query's staged path)
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
-                       ZeroOut z = ZeroOut());
+                       ZeroOut z = ZeroOut(), bool split = false);
 int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                  ps_bins bins, float* d_h, cudaStream_t s);
 int run_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_sdm_spec spec,
             uint64_t* d_hist, uint64_t* d_meta, cudaStream_t s);
+int run_cluster(ps_grid* g, const float* dsrf, ps_cluster_spec spec, uint32_t* d_label, uint64_t* d_size_hist,
+                uint64_t* d_interior_hist, uint64_t* d_meta, cudaStream_t s);
 int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                   ps_bins bins, const float* d_G, float* d_grad, float* d_grad_s, cudaStream_t s);
 

@@ -339,9 +339,14 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
       // k-th distance go to the lane's column of the insertion queue, drained after each half-batch
       // (the sorted insertion then runs with most lanes active instead of once per candidate
       // whenever any lane needs it).
-      const bool valid = lane < cnt;
+      // L lanes per central (dense clusters): lane sub of a central tests the pairs t = sub mod L
+      const uint32_t L = lanes_per_central(n_cand, a.nstart[ng.n_cells], ng.n_cells, a.stencil);
+      const uint32_t lg = L == 4u ? 2u : (L == 2u ? 1u : 0u);
+      const uint32_t sub = lane & (L - 1u), ci = lane >> lg;
+      const uint32_t n_it = 8u >> lg;  // pair tests per lane per half-batch
+      const bool valid = ci < cnt;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid) p = a.crec[c0 + lane];
+      if (valid) p = a.crec[c0 + ci];
       const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
       const float emax = valid ? H.Emax : -INFINITY;  // lanes without a central never hit
       const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
@@ -367,7 +372,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           uint32_t qn = 0;  // entries in this lane's queue column
           const float thr = top[KK - 1];
 #pragma unroll 4
-          for (int t = 8 * half; t < 8 * half + 8; ++t) {
+          for (uint32_t u = 0; u < n_it; ++u) {
+            const uint32_t t = 8 * half + u * L + sub;
             const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
             const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
             float d2a, d2b;
@@ -410,7 +416,21 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
         }
       }
-      if (valid) {
+      // merge the partial lists of the L lanes of each central (disjoint candidate subsets)
+      for (uint32_t o = 1; o < L; o <<= 1) {
+        within += __shfl_xor_sync(0xffffffffu, within, o);
+        if (KMAX > 0) {
+          float other[KK];
+#pragma unroll
+          for (int t = 0; t < KK; ++t) other[t] = __shfl_xor_sync(0xffffffffu, top[t], o);
+#pragma unroll
+          for (int t = 0; t < KK; ++t) {
+            if (!(other[t] < top[KK - 1])) break;  // the partner's list is sorted
+            topk_insert(top, other[t]);
+          }
+        }
+      }
+      if (valid && sub == 0) {
         if (a.nwithin) a.nwithin[pidx] = within;
         if (KMAX > 0)
           for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
@@ -743,7 +763,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   if (rdf) z.p[1] = d_rdf, z.n[1] = bins.n_bins;
   if (n_k) z.p[2] = d_knn, z.n[2] = n_k * bins.n_bins;
 
-  int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z);
+  int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z, true);
   if (rc) return rc;
 
   // staging budget of the CTA kernel: two CTAs per SM

@@ -27,7 +27,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kN = PS_STATIC_MAX_IONS;
 constexpr size_t kCells = kN / 8 > 65536 ? kN / 8 : 65536;  // same cell capacity rule as ps_grid_create
 constexpr size_t kTiles = (kCells + 4095) / 4096;
-constexpr size_t kItems = kCells + kN / 32 + 2;
+constexpr size_t kItems = kCells + kN / 8 + 2;  // same item capacity rule as ps_grid_create
 
 // byte offsets of every scratch buffer inside the array
 constexpr size_t o_sel = 0;
