@@ -84,16 +84,16 @@ constexpr uint32_t kHeavy = 16;
 constexpr uint32_t kSparseCand = 64;
 
 // Lanes that share one central's candidates in the query's staged path: 1, or 2 / 4 for cells
-// whose stencil holds at least 32 / 64 times the cloud's mean number of candidates (n_nbr
-// records over n_cells cells, (2s+1)^3 cells per stencil), so that the items of extreme
-// clusters do not set the kernel's length on their own (on a saturated GPU the split costs
-// more instructions than it saves).  Integer arithmetic: the central-list scan and the query
-// compute the same value.
+// whose stencil holds at least 16 / 32 times the cloud's mean number of candidates (n_nbr
+// records over n_cells cells, (2s+1)^3 cells per stencil), so that the items of dense
+// clusters do not set the kernel's length on their own (measured on the precipitate needle:
+// lower thresholds cost more instructions than the shorter tail saves, higher ones leave the
+// tail).  Integer arithmetic: the central-list scan and the query compute the same value.
 __host__ __device__ __forceinline__ uint32_t lanes_per_central(uint32_t n_cand, uint32_t n_nbr, uint32_t n_cells,
                                                                int stencil) {
   const uint64_t w = (uint64_t)(2 * stencil + 1) * (2 * stencil + 1) * (2 * stencil + 1);
   const uint64_t lhs = (uint64_t)n_cand * n_cells, unit = w * n_nbr;
-  return lhs >= 64 * unit ? 4u : (lhs >= 32 * unit ? 2u : 1u);
+  return lhs >= 32 * unit ? 4u : (lhs >= 16 * unit ? 2u : 1u);
 }
 
 // item i of a list whose heavy items grow from the front and light items from the back
