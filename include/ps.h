@@ -340,7 +340,7 @@ PS_API int ps_shuffle_labels(const uint8_t* type_in, uint8_t* type_out, int64_t 
  * reserve all device memory up front and cannot afford the device-wide
  * synchronisation of cudaMalloc/cudaFree.
  *   - Scratch is one file-scope device array sized for PS_STATIC_MAX_IONS
- *     ions (about 13 MB), held on every GPU that uses the library until the
+ *     ions (about 14 MB), held on every GPU that uses the library until the
  *     process exits.  No cudaMalloc, cudaFree or other allocating routine is
  *     called.
  *   - The first call on a device (with that device current) looks up the

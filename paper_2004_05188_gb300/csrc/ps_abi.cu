@@ -85,7 +85,8 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   const int64_t cap0 = g->stencil == 2 ? g->n_max : g->n_max / 8;
   const int64_t cap = cap0 > 65536 ? cap0 : 65536;
   g->cell_cap = (uint32_t)(cap < (int64_t)1 << 31 ? cap : (int64_t)1 << 31);
-  g->scan_tiles_cap = (g->cell_cap + 4095) / 4096;
+  // scan tiles of 4096 cells or 4096 records (the central list's record compaction)
+  g->scan_tiles_cap = (uint32_t)(((int64_t)g->cell_cap > g->n_max + 1 ? (int64_t)g->cell_cap : g->n_max + 1) + 4095) / 4096;
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
   if (e != cudaSuccess) {

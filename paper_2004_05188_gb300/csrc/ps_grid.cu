@@ -109,7 +109,7 @@ __global__ void k_reset(Geo* geo) {
     }
     geo->n_sel = 0;
     geo->status = 0;
-    geo->work_n = geo->work_n2 = geo->work_n3 = 0;
+    geo->work_n = geo->work_n2 = geo->work_n3 = geo->work_n4 = 0;
     geo->work_next = geo->work_next2 = geo->work_next3 = 0;
   }
 }
@@ -346,7 +346,7 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     *cgeo = *ngeo;
     cgeo->n_sel = 0;
     cgeo->status = 0;
-    cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = 0;
+    cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = cgeo->work_n4 = 0;
     cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
   }
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -406,8 +406,11 @@ __device__ __forceinline__ uint32_t stencil_count(const uint32_t* __restrict__ n
 
 // Warp items of a cell with n centrals: n <= 3 gives one item (the lanes of
 // the warp split the candidates of each central); otherwise ceil(n/32)
-// balanced batches of at most 32 centrals (one lane per central).
-// With L lanes per central an item holds at most 32 / L centrals.
+// batches of at most 32 centrals (one lane per central).  With L lanes per
+// central an item holds at most 32 / L centrals.  Balanced batches for the
+// kernels that give every central one lane; for the exact query (`split`)
+// full batches of 32 / L and one remainder, whose centrals then get
+// item_lanes(remainder) lanes each.
 __device__ __forceinline__ uint32_t items_of(uint32_t n, uint32_t L = 1) {
   const uint32_t per = 32u / L;
   return n == 0 ? 0u : (n <= 3 ? 1u : (n + per - 1u) / per);
@@ -425,22 +428,136 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   return v;
 }
 
-// Single-pass exclusive scan of the cell counts (decoupled look-back).  Tiles
-// are numbered in the order CTAs claim them, so every tile a CTA looks back at
-// belongs to a CTA that is already running or done; the wait on a predecessor
-// is bounded (reports PS_ERR_TIMEOUT) and the last CTA to finish clears the
-// look-back words for the next scan.  Also writes the end sentinel and, for the
-// central list, the work lists: cells with at least dense_min centrals go to
+// Warp 0 of the CTA that owns scan tile t (tiles are numbered in the order CTAs
+// claim them, so every tile it looks back at belongs to a CTA that is already
+// running or done): publishes the tile's aggregate, looks back 32 predecessors
+// at a time (lane l reads tile j - l; the window is summed up to the nearest tile
+// that holds an inclusive prefix; the virtual tile -1 holds prefix 0), publishes
+// the inclusive prefix and returns the exclusive one in every lane.  A wait on a
+// predecessor gives up after kWaitLimitNs and records PS_ERR_TIMEOUT in *status.
+__device__ uint32_t tile_lookback(uint32_t t, uint32_t total, unsigned long long* state, int* status) {
+  const uint32_t lane = lane_id();
+  uint32_t prefix = 0;
+  if (t > 0) {
+    if (lane == 0) st_release(&state[t], kFlagA | total);
+    int j = (int)t - 1;
+    uint64_t t0 = 0;
+    while (j >= 0) {
+      const int idx = j - (int)lane;
+      const unsigned long long w = idx >= 0 ? ld_acquire(&state[idx]) : kFlagP;
+      const uint32_t isP = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+      const uint32_t notready = __ballot_sync(0xffffffffu, (w >> 62) == 0);
+      const uint32_t lim = isP ? (uint32_t)(__ffs(isP) - 1) : 31u;
+      const uint32_t need = lim == 31u ? 0xffffffffu : ((2u << lim) - 1u);
+      if (notready & need) {
+        int give_up = 0;
+        if (lane == 0) {
+          if (t0 == 0) t0 = global_ns();
+          give_up = global_ns() - t0 > kWaitLimitNs;
+        }
+        if (__shfl_sync(0xffffffffu, give_up, 0)) {
+          if (lane == 0) atomicCAS(status, 0, (int)PS_ERR_TIMEOUT);
+          break;
+        }
+        continue;
+      }
+      uint32_t v = lane <= lim ? (uint32_t)w : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      prefix += v;
+      if (isP) break;
+      j -= 32;
+      t0 = 0;
+    }
+  }
+  if (lane == 0) st_release(&state[t], kFlagP | (uint32_t)(prefix + total));
+  return prefix;
+}
+
+// End of a single-pass scan (thread 0 of every CTA): the last CTA to finish clears
+// the look-back words and the tile counter for the next scan.
+__device__ void scan_finish(unsigned long long* state, uint32_t* ctr, uint32_t tiles) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {
+      for (uint32_t i = 0; i < tiles; ++i) state[i] = 0ull;
+      ctr[0] = 0;
+      __threadfence();
+      ctr[1] = 0;
+    }
+  }
+}
+
+// Work lists of the central list for the kScanItems cells c0.. with v[k] centrals
+// (every lane of the warp calls it): cells with at least dense_min centrals go to
 // `work` (CTA kernel), the others are split into warp items (cell,
 // first << 6 | count): sparse cells (fewer than kHeavy centrals and at most
-// kSparseCand candidates in the stencil of the neighbour grid `nstart`) from
-// the back of `witem`, the rest from the front, in batches of at most
-// 32 / lanes_per_central centrals when `split` is set.
+// kSparseCand candidates in the stencil of the neighbour grid `nstart`) from the
+// back of `witem`, the rest from the front.  With `split` (the exact query),
+// batches of 32 / lanes_per_central centrals and one remainder, and the very heavy
+// items (very_heavy) in `whi` instead of the front of `witem`; otherwise balanced
+// batches of at most 32.
+__device__ __forceinline__ void emit_items(const uint32_t (&v)[kScanItems], uint32_t c0, uint32_t nc, Geo* geo,
+                                           uint32_t* __restrict__ work, uint2* __restrict__ witem, uint32_t dense_min,
+                                           uint32_t cap, const uint32_t* __restrict__ nstart, int stencil, bool split,
+                                           uint2* __restrict__ whi) {
+  uint32_t n_front = 0, n_back = 0, n_hi = 0;
+  bool sparse[kScanItems];
+  uint32_t lanes[kScanItems], cands[kScanItems];
+  const uint32_t n_nbr = nstart != nullptr ? nstart[nc] : 0u;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const bool dense = (c0 + k < nc) && v[k] >= dense_min;
+    const uint32_t s1 = warp_append(dense, &geo->work_n);
+    if (dense) work[s1] = c0 + k;
+    const uint32_t cand = (!dense && v[k] > 0 && nstart != nullptr) ? stencil_count(nstart, geo, c0 + k, stencil) : 0u;
+    sparse[k] = !dense && v[k] > 0 && v[k] < kHeavy && nstart != nullptr && cand <= kSparseCand;
+    lanes[k] = (split && !sparse[k] && v[k] > 3) ? lanes_per_central(cand, n_nbr, nc, stencil) : 1u;
+    cands[k] = cand;
+    if (!dense && sparse[k]) n_back += items_of(v[k], lanes[k]);
+    if (!dense && !sparse[k]) {
+      const uint32_t m = items_of(v[k], lanes[k]), per = 32u / lanes[k];
+      for (uint32_t q = 0, first = 0; q < m; ++q) {
+        const uint32_t cnt = split ? min(per, v[k] - first) : 0u;
+        const bool hi = whi != nullptr && cnt > 3 && very_heavy(cand, item_lanes(cnt), n_nbr, nc, stencil);
+        (hi ? n_hi : n_front) += 1;
+        first += cnt;
+      }
+    }
+  }
+  uint32_t hs = warp_append_n(n_front, &geo->work_n2);
+  uint32_t ls = warp_append_n(n_back, &geo->work_n3);
+  uint32_t xs = warp_append_n(n_hi, &geo->work_n4);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (v[k] >= dense_min) continue;
+    const uint32_t m = items_of(v[k], lanes[k]);
+    if (m == 0) continue;
+    const uint32_t base = v[k] / m, rem = v[k] % m, per = 32u / lanes[k];
+    uint32_t first = 0;
+    for (uint32_t q = 0; q < m; ++q) {
+      const uint32_t cnt = split ? min(per, v[k] - first) : base + (q < rem ? 1u : 0u);
+      const uint2 it = make_uint2(c0 + k, (first << 6) | cnt);
+      if (sparse[k])
+        witem[cap - 1 - ls++] = it;
+      else if (whi != nullptr && split && cnt > 3 && very_heavy(cands[k], item_lanes(cnt), n_nbr, nc, stencil))
+        whi[xs++] = it;
+      else
+        witem[hs++] = it;
+      first += cnt;
+    }
+  }
+}
+
+// Single-pass exclusive scan of the cell counts (decoupled look-back).  Also
+// writes the end sentinel and, for the central list (`work` given), the work
+// lists (emit_items).
 __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ count, Geo* geo,
                                                        uint32_t* __restrict__ start, uint32_t* __restrict__ work,
                                                        uint2* __restrict__ witem, uint32_t dense_min, uint32_t cap,
                                                        unsigned long long* state, uint32_t* ctr,
-                                                       const uint32_t* __restrict__ nstart, int stencil, bool split) {
+                                                       const uint32_t* __restrict__ nstart, int stencil, bool split,
+                                                       uint2* __restrict__ whi) {
   griddep_wait();
   griddep_launch();
   __shared__ uint32_t s_warp[32];
@@ -462,45 +579,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
     uint32_t total;
     const uint32_t excl = block_exclusive_scan(sum, s_warp, total);
     if (threadIdx.x < 32) {
-      // warp 0 looks back 32 predecessors at a time: lane l reads tile j - l; the
-      // window is summed up to the nearest tile that holds an inclusive prefix
-      // (the virtual tile -1 holds prefix 0)
-      const uint32_t lane = lane_id();
-      uint32_t prefix = 0;
-      if (t > 0) {
-        if (lane == 0) st_release(&state[t], kFlagA | total);
-        int j = (int)t - 1;
-        uint64_t t0 = 0;
-        while (j >= 0) {
-          const int idx = j - (int)lane;
-          const unsigned long long w = idx >= 0 ? ld_acquire(&state[idx]) : kFlagP;
-          const uint32_t isP = __ballot_sync(0xffffffffu, (w >> 62) == 2);
-          const uint32_t notready = __ballot_sync(0xffffffffu, (w >> 62) == 0);
-          const uint32_t lim = isP ? (uint32_t)(__ffs(isP) - 1) : 31u;
-          const uint32_t need = lim == 31u ? 0xffffffffu : ((2u << lim) - 1u);
-          if (notready & need) {
-            int give_up = 0;
-            if (lane == 0) {
-              if (t0 == 0) t0 = global_ns();
-              give_up = global_ns() - t0 > kWaitLimitNs;
-            }
-            if (__shfl_sync(0xffffffffu, give_up, 0)) {
-              if (lane == 0) atomicCAS(&geo->status, 0, (int)PS_ERR_TIMEOUT);
-              break;
-            }
-            continue;
-          }
-          uint32_t v = lane <= lim ? (uint32_t)w : 0u;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          prefix += v;
-          if (isP) break;
-          j -= 32;
-          t0 = 0;
-        }
-      }
-      if (lane == 0) {
-        st_release(&state[t], kFlagP | (uint32_t)(prefix + total));
+      const uint32_t prefix = tile_lookback(t, total, state, &geo->status);
+      if (lane_id() == 0) {
         s_prefix = prefix;
         if (t == tiles - 1) start[nc] = prefix + total;  // end sentinel: number of records
       }
@@ -512,51 +592,121 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
       if (c0 + k < nc) start[c0 + k] = run;
       run += v[k];
     }
-    if (work != nullptr) {
-      uint32_t n_front = 0, n_back = 0;
-      bool sparse[kScanItems];
-      uint32_t lanes[kScanItems];
-      const uint32_t n_nbr = nstart != nullptr ? nstart[nc] : 0u;
+    if (work != nullptr) emit_items(v, c0, nc, geo, work, witem, dense_min, cap, nstart, stencil, split, whi);
+    __syncthreads();  // s_tile and s_prefix are rewritten next
+  }
+  scan_finish(state, ctr, tiles);
+}
+
+// Central list of a central type set contained in the neighbour set, step 1 of 2.
+// The centrals are then a subset of the neighbour records, which are already
+// sorted by cell: an order-preserving compaction of those records (single-pass
+// scan of the central flags over the records) gives the sorted central records
+// directly, with no second pass over the whole cloud and no counting sort.  pfx[j]
+// = number of centrals among records 0..j-1 (pfx[n_records] = all), from which
+// k_central_items reads the cell starts.  Also resets the central list's geometry
+// and counters and zeroes the query's outputs.
+__global__ void __launch_bounds__(kScanThreads) k_central_subset(const float4* __restrict__ nrec,
+                                                                 const Geo* __restrict__ ngeo, Geo* cgeo,
+                                                                 const uint8_t* __restrict__ type,
+                                                                 const float* __restrict__ dsrf, Mask mask,
+                                                                 float dsrf_min, float4* __restrict__ crec,
+                                                                 uint32_t* __restrict__ pfx, unsigned long long* state,
+                                                                 uint32_t* ctr, ZeroOut z) {
+  griddep_wait();
+  griddep_launch();
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_tile, s_prefix;
+  const uint32_t nr = ngeo->n_sel;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // every field but n_sel, which the thread that scans the last tile writes
+    for (int a = 0; a < 3; ++a) cgeo->origin[a] = ngeo->origin[a], cgeo->dims[a] = ngeo->dims[a];
+    for (int a = 0; a < 6; ++a) cgeo->bbox_key[a] = ngeo->bbox_key[a];
+    cgeo->inv_h = ngeo->inv_h;
+    cgeo->h = ngeo->h;
+    cgeo->n_cells = ngeo->n_cells;
+    cgeo->status = 0;
+    cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = cgeo->work_n4 = 0;
+    cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
+    if (nr == 0) pfx[0] = 0, cgeo->n_sel = 0;
+  }
+  {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int k = 0; k < 3; ++k)
+      if (z.p[k])
+        for (uint32_t i = tid; i < z.n[k]; i += stride) z.p[k][i] = 0ull;
+  }
+  const uint32_t tiles = (nr + kScanTile - 1) / kScanTile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[0], 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= tiles) break;
+    const uint32_t j0 = t * kScanTile + threadIdx.x * kScanItems;
+    float4 r[kScanItems];
+    uint32_t f[kScanItems], sum = 0;
 #pragma unroll
-      for (int k = 0; k < kScanItems; ++k) {
-        const bool dense = (c0 + k < nc) && v[k] >= dense_min;
-        const uint32_t s1 = warp_append(dense, &geo->work_n);
-        if (dense) work[s1] = c0 + k;
-        const uint32_t cand = (!dense && v[k] > 0 && nstart != nullptr) ? stencil_count(nstart, geo, c0 + k, stencil) : 0u;
-        sparse[k] = !dense && v[k] > 0 && v[k] < kHeavy && nstart != nullptr && cand <= kSparseCand;
-        lanes[k] = (split && !sparse[k] && v[k] > 3) ? lanes_per_central(cand, n_nbr, nc, stencil) : 1u;
-        if (!dense) (sparse[k] ? n_back : n_front) += items_of(v[k], lanes[k]);
+    for (int k = 0; k < kScanItems; ++k) {
+      f[k] = 0;
+      if (j0 + k < nr) {
+        r[k] = nrec[j0 + k];
+        const uint32_t idx = __float_as_uint(r[k].w);
+        f[k] = (in_mask(mask, type[idx]) && (dsrf == nullptr || dsrf[idx] >= dsrf_min)) ? 1u : 0u;
       }
-      uint32_t hs = warp_append_n(n_front, &geo->work_n2);
-      uint32_t ls = warp_append_n(n_back, &geo->work_n3);
+      sum += f[k];
+    }
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan(sum, s_warp, total);
+    if (threadIdx.x < 32) {
+      const uint32_t prefix = tile_lookback(t, total, state, &cgeo->status);
+      if (lane_id() == 0) {
+        s_prefix = prefix;
+        if (t == tiles - 1) pfx[nr] = prefix + total, cgeo->n_sel = prefix + total;
+      }
+    }
+    __syncthreads();
+    uint32_t run = s_prefix + excl;
 #pragma unroll
-      for (int k = 0; k < kScanItems; ++k) {
-        if (v[k] >= dense_min) continue;
-        const uint32_t m = items_of(v[k], lanes[k]);
-        if (m == 0) continue;
-        const uint32_t base = v[k] / m, rem = v[k] % m;
-        uint32_t first = 0;
-        for (uint32_t q = 0; q < m; ++q) {
-          const uint32_t cnt = base + (q < rem ? 1u : 0u);
-          const uint2 it = make_uint2(c0 + k, (first << 6) | cnt);
-          if (sparse[k])
-            witem[cap - 1 - ls++] = it;
-          else
-            witem[hs++] = it;
-          first += cnt;
-        }
+    for (int k = 0; k < kScanItems; ++k) {
+      if (j0 + k < nr) {
+        pfx[j0 + k] = run;
+        if (f[k]) crec[run] = r[k];
       }
+      run += f[k];
     }
     __syncthreads();  // s_tile and s_prefix are rewritten next
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {
-      for (uint32_t i = 0; i < tiles; ++i) state[i] = 0ull;
-      ctr[0] = 0;
-      __threadfence();
-      ctr[1] = 0;
+  scan_finish(state, ctr, tiles);
+}
+
+// Central list of a central type set contained in the neighbour set, step 2 of 2:
+// cell starts from the record prefix (a cell's centrals are the flagged records
+// among its neighbour records), the end sentinel and the work lists.
+__global__ void __launch_bounds__(kThreads) k_central_items(const uint32_t* __restrict__ nstart,
+                                                            const uint32_t* __restrict__ pfx, Geo* cgeo,
+                                                            uint32_t* __restrict__ start, uint32_t* __restrict__ work,
+                                                            uint2* __restrict__ witem, uint32_t dense_min, uint32_t cap,
+                                                            int stencil, bool split, uint2* __restrict__ whi) {
+  griddep_wait();
+  griddep_launch();
+  const uint32_t nc = cgeo->n_cells;
+  const uint32_t step = gridDim.x * blockDim.x * kScanItems;
+  // the loop bound is uniform per block: every lane reaches the warp-wide appends
+  for (uint32_t base = blockIdx.x * blockDim.x * kScanItems; base < nc; base += step) {
+    const uint32_t c0 = base + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = 0;
+      const uint32_t c = c0 + k;
+      if (c < nc) {
+        const uint32_t b = pfx[nstart[c]], e = pfx[nstart[c + 1]];
+        start[c] = b;
+        v[k] = e - b;
+        if (c == nc - 1) start[nc] = e;
+      }
     }
+    emit_items(v, c0, nc, cgeo, work, witem, dense_min, cap, nstart, stencil, split, whi);
   }
 }
 
@@ -587,14 +737,14 @@ static int scan_cells(ps_grid* g, CellList& L, Geo* geo, bool with_work, cudaStr
             PS_CUDA(launch_pdl(k_scan, grid_blocks(g, 1), kScanThreads, 0, s, L.count, geo, L.start, with_work ? L.work : nullptr,
                                                                L.witem, g->dense_min, g->item_cap, g->scan_state,
                                                                g->scan_ctr, with_work ? g->nbr.start : nullptr,
-                                                               g->stencil, split)));
+                                                               g->stencil, split, split ? g->nbr_witem : nullptr)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
 int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cudaStream_t s) {
   Mask m;
-  for (int w = 0; w < 4; ++w) m.w[w] = nbr_mask[w];
+  for (int w = 0; w < 4; ++w) m.w[w] = nbr_mask[w], g->nbr_mask[w] = nbr_mask[w];
   Geo* geo = g->nbr.geo;
   const bool vec = aligned16(g->type) && aligned16(g->xyz);
   PS_LAUNCH(PS_KID_RESET, s, PS_CUDA(launch_pdl(k_reset, 1, 32, 0, s, geo)));
@@ -616,7 +766,21 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
                        ZeroOut z, bool split) {
   Mask m;
-  for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w];
+  bool subset = !g->pack_type;
+  for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w], subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
+  if (subset) {
+    // centrals are neighbour records: compact the cell-sorted records (2 kernels)
+    uint32_t* pfx = reinterpret_cast<uint32_t*>(g->cr);  // 2 n_max words, n_records + 1 needed
+    PS_LAUNCH(PS_KID_CENTRAL, s,
+              PS_CUDA(launch_pdl(k_central_subset, grid_blocks(g, 1), kScanThreads, 0, s, g->nbr.rec, g->nbr.geo,
+                                 g->ctr.geo, g->type, dsrf, m, dsrf_min, g->ctr.rec, pfx, g->scan_state, g->scan_ctr, z)));
+    PS_LAUNCH(PS_KID_SCAN, s,
+              PS_CUDA(launch_pdl(k_central_items, grid_blocks(g, 4), kThreads, 0, s, g->nbr.start, pfx, g->ctr.geo,
+                                 g->ctr.start, g->ctr.work, g->ctr.witem, g->dense_min, g->item_cap, g->stencil, split,
+                                 split ? g->nbr_witem : nullptr)));
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+  }
   const bool vec = aligned16(g->type) && aligned16(g->xyz) && (dsrf == nullptr || aligned16(dsrf));
   PS_LAUNCH(PS_KID_CENTRAL, s,
             PS_CUDA(launch_pdl(k_central_reset, grid_blocks(g, 4), kThreads, 0, s, g->nbr.geo, g->ctr.geo, g->ctr.count, z)));

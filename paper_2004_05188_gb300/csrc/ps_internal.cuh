@@ -75,6 +75,7 @@ struct Geo {
   uint32_t work_next2;
   uint32_t work_n3;    // items from the back of witem[] (sparse cells of central lists), witem[cap-1] downwards
   uint32_t work_next3; // light items taken so far (query kernel: 32 at a time)
+  uint32_t work_n4;    // very heavy warp items (exact query), listed apart and taken before the others
 };
 
 // Warp items with at least this many centrals per cell are listed first (largest work first).
@@ -94,6 +95,23 @@ __host__ __device__ __forceinline__ uint32_t lanes_per_central(uint32_t n_cand, 
   const uint64_t w = (uint64_t)(2 * stencil + 1) * (2 * stencil + 1) * (2 * stencil + 1);
   const uint64_t lhs = (uint64_t)n_cand * n_cells, unit = w * n_nbr;
   return lhs >= 32 * unit ? 4u : (lhs >= 16 * unit ? 2u : 1u);
+}
+
+// Lanes per central of a warp item of the exact query with cnt (4..32) centrals: the largest
+// power of two, at most 8, with cnt * L <= 32.  A full item of a cell split by
+// lanes_per_central (32 / L centrals) gets that L back; a cell's last, partial item gets more
+// lanes, so that its warp is not left mostly idle.
+__host__ __device__ __forceinline__ uint32_t item_lanes(uint32_t cnt) {
+  return cnt <= 4u ? 8u : (cnt <= 8u ? 4u : (cnt <= 16u ? 2u : 1u));
+}
+
+// A warp item of the exact query is "very heavy" when each of its lanes tests at least 8 times
+// the cloud's mean stencil population (n_cand / L >= 8 w n_nbr / n_cells): those items are
+// listed apart and taken first, so that the query's last items are short ones (longest first).
+__host__ __device__ __forceinline__ bool very_heavy(uint32_t n_cand, uint32_t L, uint32_t n_nbr, uint32_t n_cells,
+                                                    int stencil) {
+  const uint64_t w = (uint64_t)(2 * stencil + 1) * (2 * stencil + 1) * (2 * stencil + 1);
+  return (uint64_t)n_cand * n_cells >= 8 * (uint64_t)L * w * n_nbr;
 }
 
 // item i of a list whose heavy items grow from the front and light items from the back
@@ -131,9 +149,10 @@ struct ps_grid {
   uint32_t item_cap = 0;       // capacity of the warp item list
   int stencil = 1;             // neighbour cells searched on each side (1: cell >= r_cut, 2: cell >= r_cut/2)
   bool pack_type = false;      // records carry (index << 8 | type) instead of the index (batched sweeps)
+  uint64_t nbr_mask[4] = {0, 0, 0, 0};  // type set of the last build's neighbour records
   uint32_t* sel = nullptr;     // [n_max] selected ion indices
   uint2* cr = nullptr;         // [n_max] (cell, rank) of selected ions
-  unsigned long long* scan_state = nullptr;  // [scan tiles] look-back words of the single-pass scan
+  unsigned long long* scan_state = nullptr;  // [scan tiles] look-back words of the single-pass scans (cells, records)
   uint32_t* scan_ctr = nullptr;              // [2] tile counter, finished-block counter
   uint32_t scan_tiles_cap = 0;
   // smoothed RDF scratch (fine grid of at most kSoftFineMax bins)

@@ -40,6 +40,7 @@ struct QueryArgs {
   const uint32_t* cstart;
   const uint32_t* cwork;
   const uint2* witem;
+  const uint2* whi;   // very heavy items (taken before those of witem)
   uint32_t work_cap;  // capacity of witem (light items grow from its end)
   Geo* cgeo;
   int stencil;
@@ -206,10 +207,19 @@ struct Hist {
     __syncwarp();
   }
 
-  // add the shared counters to the global histograms and clear them (whole CTA)
+  // add the shared counters to the global histograms and clear them (whole CTA); the
+  // per-warp rows are summed in the CTA first, one global atomic per bin and CTA
   __device__ void flush(const QueryArgs& a) {
-    flush_warp(a);
     __syncthreads();
+    if (RDF && priv) {
+      uint32_t* rows = reinterpret_cast<uint32_t*>(s_rdf);
+      const uint32_t nw = blockDim.x >> 5;
+      for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+        unsigned long long sum = 0;
+        for (uint32_t w = 0; w < nw; ++w) sum += rows[w * nb + b], rows[w * nb + b] = 0;
+        if (sum) atomicAdd((unsigned long long*)&a.rdf[b], sum);
+      }
+    }
     if (RDF && !priv)
       for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
         if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], s_rdf[b]), s_rdf[b] = 0;
@@ -222,15 +232,25 @@ struct Hist {
   }
 };
 
+// pair counters of the whole CTA (every thread calls it): summed in the warp, then in shared
+// memory, one global atomic per counter and CTA
 __device__ __forceinline__ void add_pair_counters(const QueryArgs& a, uint64_t binned, uint64_t below) {
+  __shared__ unsigned long long s_pc[2];
+  if (threadIdx.x == 0) s_pc[0] = 0, s_pc[1] = 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     binned += __shfl_xor_sync(0xffffffffu, binned, o);
     below += __shfl_xor_sync(0xffffffffu, below, o);
   }
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
-    if (binned) atomicAdd((unsigned long long*)&a.meta[PS_META_N_PAIRS], (unsigned long long)binned);
-    if (below) atomicAdd((unsigned long long*)&a.meta[PS_META_N_BELOW], (unsigned long long)below);
+    if (binned) atomicAdd(&s_pc[0], (unsigned long long)binned);
+    if (below) atomicAdd(&s_pc[1], (unsigned long long)below);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_pc[0]) atomicAdd((unsigned long long*)&a.meta[PS_META_N_PAIRS], s_pc[0]);
+    if (s_pc[1]) atomicAdd((unsigned long long*)&a.meta[PS_META_N_BELOW], s_pc[1]);
   }
 }
 
@@ -264,9 +284,10 @@ __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, IN
 
 // ---------------------------------------------------------------------------
 // warp kernel
-//   heavy items (cells with >= kHeavy centrals, batches of 8..32 centrals): one
-//     lane per central, the candidates staged 32 at a time in the warp's shared
-//     buffer and tested two at a time with packed float32 math;
+//   heavy items (cells with >= kHeavy centrals, batches of 4..32 centrals): one
+//     to eight lanes per central (item_lanes), the candidates staged 32 at a
+//     time in the warp's shared buffer and tested two at a time with packed
+//     float32 math;
 //   light items (cells with < kHeavy centrals): the warp takes 32 items at a
 //     time and gives each of their centrals a thread of its own that walks its
 //     own stencil (the records of neighbouring centrals' cells hit in L1).
@@ -289,7 +310,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
   const Geo ng = *a.ngeo;
-  const uint32_t n_front = a.cgeo->work_n2, n_light = a.cgeo->work_n3;
+  const uint32_t n_hi = a.cgeo->work_n4, n_front = n_hi + a.cgeo->work_n2, n_light = a.cgeo->work_n3;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   uint64_t my_binned = 0, my_below = 0;
   float4* buf = s_buf[w];
@@ -298,13 +319,13 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   uint32_t* rsrc = s_rsrc[w];
   uint32_t* rpre = s_rpre[w];
 
-  // ---- items from the front: dense cells ----
+  // ---- items from the front: dense cells, the very heavy ones first ----
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(&a.cgeo->work_next2, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_front) break;
-    const uint2 it = a.witem[item];
+    const uint2 it = item < n_hi ? a.whi[item] : a.witem[item - n_hi];
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.cstart[c] + first;
     // run table: sources and prefix counts of the candidate runs
@@ -339,9 +360,10 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
       // k-th distance go to the lane's column of the insertion queue, drained after each half-batch
       // (the sorted insertion then runs with most lanes active instead of once per candidate
       // whenever any lane needs it).
-      // L lanes per central (dense clusters): lane sub of a central tests the pairs t = sub mod L
-      const uint32_t L = lanes_per_central(n_cand, a.nstart[ng.n_cells], ng.n_cells, a.stencil);
-      const uint32_t lg = L == 4u ? 2u : (L == 2u ? 1u : 0u);
+      // L lanes per central (items of dense clusters, a cell's partial last item): lane sub of a
+      // central tests the pairs t = sub mod L
+      const uint32_t L = item_lanes(cnt);
+      const uint32_t lg = L == 8u ? 3u : (L == 4u ? 2u : (L == 2u ? 1u : 0u));
       const uint32_t sub = lane & (L - 1u), ci = lane >> lg;
       const uint32_t n_it = 8u >> lg;  // pair tests per lane per half-batch
       const bool valid = ci < cnt;
@@ -366,12 +388,12 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         }
         __syncwarp();
         nxt = fetch(b + 32 + lane, rr);
-#pragma unroll
+#pragma unroll 1
         for (int half = 0; half < 2; ++half) {
           uint32_t nh = 0;  // hits in the warp list (uniform)
           uint32_t qn = 0;  // entries in this lane's queue column
           const float thr = top[KK - 1];
-#pragma unroll 4
+#pragma unroll 2
           for (uint32_t u = 0; u < n_it; ++u) {
             const uint32_t t = 8 * half + u * L + sub;
             const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
@@ -416,10 +438,24 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
         }
       }
-      // merge the partial lists of the L lanes of each central (disjoint candidate subsets)
+      // merge the partial lists of the L lanes of each central (disjoint candidate subsets); the
+      // partner's sorted list is read from the warp's queue buffer in a rolled loop, which keeps
+      // the kernel's code small (its speed depends on the instruction cache)
       for (uint32_t o = 1; o < L; o <<= 1) {
         within += __shfl_xor_sync(0xffffffffu, within, o);
-        if (KMAX > 0) {
+        if constexpr (KMAX > 0 && KK * 32 <= 32 * kHalf) {
+          __syncwarp();
+#pragma unroll
+          for (int t = 0; t < KK; ++t) kq[t * 32 + lane] = top[t];
+          __syncwarp();
+          const float* ot = kq + (lane ^ o);
+#pragma unroll 1
+          for (int t = 0; t < KK; ++t) {
+            const float v = ot[t * 32];
+            if (!(v < top[KK - 1])) break;  // the partner's list is sorted
+            topk_insert(top, v);
+          }
+        } else if constexpr (KMAX > 0) {
           float other[KK];
 #pragma unroll
           for (int t = 0; t < KK; ++t) other[t] = __shfl_xor_sync(0xffffffffu, top[t], o);
@@ -720,6 +756,7 @@ static int dispatch_k(const ps_grid* g, const QueryArgs& qa, uint32_t sc, uint32
   if (k <= 2) return launch_query<2, RDF>(g, qa, sc, sw, s);
   if (k <= 4) return launch_query<4, RDF>(g, qa, sc, sw, s);
   if (k <= 8) return launch_query<8, RDF>(g, qa, sc, sw, s);
+  if (k <= 10) return launch_query<10, RDF>(g, qa, sc, sw, s);
   if (k <= 12) return launch_query<12, RDF>(g, qa, sc, sw, s);
   if (k <= 16) return launch_query<16, RDF>(g, qa, sc, sw, s);
   return launch_query<32, RDF>(g, qa, sc, sw, s);
@@ -737,6 +774,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.cstart = g->ctr.start;
   qa.cwork = g->ctr.work;
   qa.witem = g->ctr.witem;
+  qa.whi = g->nbr_witem;
   qa.work_cap = g->item_cap;
   qa.cgeo = g->ctr.geo;
   qa.stencil = g->stencil;

@@ -8,7 +8,7 @@
 // reserve all device memory at start-up and must not block on the implicit
 // device synchronisation of cudaMalloc/cudaFree in the loop.
 //
-// The array is sized for PS_STATIC_MAX_IONS ions (about 13 MB) and every
+// The array is sized for PS_STATIC_MAX_IONS ions (about 14 MB) and every
 // process that loads libps holds it on each GPU it uses until exit.
 #include <mutex>
 
@@ -26,7 +26,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t kN = PS_STATIC_MAX_IONS;
 constexpr size_t kCells = kN / 8 > 65536 ? kN / 8 : 65536;  // same cell capacity rule as ps_grid_create
-constexpr size_t kTiles = (kCells + 4095) / 4096;
+constexpr size_t kTiles = ((kCells > kN + 1 ? kCells : kN + 1) + 4095) / 4096;  // cells or records
 constexpr size_t kItems = kCells + kN / 8 + 2;  // same item capacity rule as ps_grid_create
 
 // byte offsets of every scratch buffer inside the array
@@ -40,7 +40,8 @@ constexpr size_t o_cstart = o_ccount + align256(kCells * 4);
 constexpr size_t o_crec = o_cstart + align256((kCells + 1) * 4);
 constexpr size_t o_cwork = o_crec + align256(kN * 16);
 constexpr size_t o_witem = o_cwork + align256(kCells * 4);
-constexpr size_t o_part = o_witem + align256(kItems * 8);
+constexpr size_t o_nwitem = o_witem + align256(kItems * 8);  // very heavy items of the query
+constexpr size_t o_part = o_nwitem + align256(kItems * 8);
 constexpr size_t o_sctr = o_part + align256(kTiles * 8);
 constexpr size_t o_ngeo = o_sctr + align256(8);
 constexpr size_t o_cgeo = o_ngeo + align256(sizeof(Geo));
@@ -108,6 +109,7 @@ extern "C" int ps_spatstat_static(const float* xyz, const uint8_t* type, const f
   g.ctr.rec = reinterpret_cast<float4*>(b + o_crec);
   g.ctr.work = reinterpret_cast<uint32_t*>(b + o_cwork);
   g.ctr.witem = reinterpret_cast<uint2*>(b + o_witem);
+  g.nbr_witem = reinterpret_cast<uint2*>(b + o_nwitem);
   g.ctr.geo = reinterpret_cast<Geo*>(b + o_cgeo);
   g.scan_state = reinterpret_cast<unsigned long long*>(b + o_part);  // zero at load; each scan clears it again
   g.scan_ctr = reinterpret_cast<uint32_t*>(b + o_sctr);
