@@ -155,11 +155,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, path: str | None = None):
+        import tempfile
+
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv"
+        # the raw samples are kept (a record beside the number); default: a temporary file
+        self.path = path or os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -708,7 +710,7 @@ def run_gpu(args, wl_name, wl):
             step()
 
     sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else
-                           int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+                           int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]), args.clocks_csv)
     sampler.start()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -908,6 +910,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="needle8m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="file for the raw nvidia-smi clock samples of the timed region "
+                                                         "(default: a temporary file)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--copy-streams", type=int, default=1, help="streams for the e2e input copies (one is fastest)")
     ap.add_argument("--serial-combos", action="store_true", help="run the type combinations one after the other "
