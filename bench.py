@@ -75,7 +75,7 @@ def load_peaks():
 
 # FP32 pipe: 152 SMs x 128 lanes, one non-fused FP32 operation per lane per clock
 N_SM, FP32_LANES = 152, 128
-FLOPS_PER_CANDIDATE = 8  # d2 = ((dx*dx) + (dy*dy)) + (dz*dz): 3 sub, 3 mul, 2 add
+FLOPS_PER_CANDIDATE = 9  # d2 = ((dx*dx) + (dy*dy)) + (dz*dz): 3 sub, 3 mul, 2 add; 1 compare against the range
 
 
 def alu_peak_tflops():
