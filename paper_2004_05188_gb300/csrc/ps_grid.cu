@@ -690,6 +690,8 @@ __global__ void __launch_bounds__(kThreads) k_central_items(const uint32_t* __re
   griddep_wait();
   griddep_launch();
   const uint32_t nc = cgeo->n_cells;
+  // after a look-back that gave up (status set) the prefixes may be inconsistent: no work items
+  const bool ok = cgeo->status == 0;
   const uint32_t step = gridDim.x * blockDim.x * kScanItems;
   // the loop bound is uniform per block: every lane reaches the warp-wide appends
   for (uint32_t base = blockIdx.x * blockDim.x * kScanItems; base < nc; base += step) {
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(kThreads) k_central_items(const uint32_t* __re
       if (c < nc) {
         const uint32_t b = pfx[nstart[c]], e = pfx[nstart[c + 1]];
         start[c] = b;
-        v[k] = e - b;
+        v[k] = (ok && e >= b) ? e - b : 0u;
         if (c == nc - 1) start[nc] = e;
       }
     }
