@@ -14,7 +14,8 @@ e2e     = the same metric through the public Python API with the inputs in
           pinned host memory: H2D copy + both combinations + D2H of results.
 roofline: the dominant kernel family, timed with CUDA events on its stream
           in the timed region, against the measured HBM copy bandwidth.
-cpu_baseline: the oracle (single-threaded C) on a bounded z-slab sample.
+cpu_baseline: the oracle (C) on a bounded z-slab sample, on every host core (one
+          z-slab of centrals per thread, exact sum), and on one core.
 
 --impl reference runs the oracle as the comparison arm on the host cores.
 """
@@ -226,6 +227,55 @@ def oracle_step(orc, cloud, wl):
     return n
 
 
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def slab_parts(xyz, t, d, frac: float, halo: float, parts: int):
+    """The z-slab of slab_sample split into `parts` consecutive z-slabs of centrals, each with its own
+    halo of neighbours: independent oracle runs over them add up to the whole slab's exact counts."""
+    z = xyz[:, 2]
+    zlo, zhi = float(z.min()), float(z.max())
+    z0 = zlo + 0.5 * (zhi - zlo) * (1.0 - frac)
+    z1 = z0 + frac * (zhi - zlo)
+    cuts = [z0 + (z1 - z0) * i / parts for i in range(parts + 1)]
+    out = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        keep = (z >= a - halo) & (z < b + halo)
+        core = (z >= a) & (z < b)
+        out.append((xyz[keep], t[keep], np.where(core[keep], d[keep], np.float32(-1e30)).astype(np.float32)))
+    return out
+
+
+def oracle_step_parts(orc, parts, wl, pool):
+    """One step of the oracle on every part, one host thread each (ctypes releases the GIL; the
+    oracle keeps no global state)."""
+    return sum(pool.map(lambda c: oracle_step(orc, c, wl), parts))
+
+
+def oracle_sample_parallel(wl, cloud, pool, cores: int, target_s=1.0):
+    """Bounded sample for the oracle on `cores` host threads: a z-slab, split in `cores` parts,
+    whose parallel run takes ~target_s."""
+    import oracle as orc
+
+    orc.build()
+    xyz, t, d = cloud
+    halo = wl["bins"][1] * wl["bins"][2]
+    frac = min(1.0, 0.02 * cores)
+    while True:
+        parts = slab_parts(xyz, t, d, frac, halo, cores)
+        t0 = time.perf_counter()
+        nq = oracle_step_parts(orc, parts, wl, pool)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * target_s or frac >= 1.0:
+            break
+        frac = min(1.0, frac * max(2.0, 0.5 * target_s / max(dt, 1e-3)))
+    return orc, parts, frac, nq, dt
+
+
 def oracle_sample(wl_name, wl, cloud, target_s=1.0):
     """Bounded sample of the workload for the oracle: a z-slab whose single-threaded run takes ~target_s."""
     import oracle as orc
@@ -244,27 +294,33 @@ def oracle_sample(wl_name, wl, cloud, target_s=1.0):
 
 
 def run_reference(args, wl_name, wl):
+    import concurrent.futures as cf
+
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cloud = make_cloud(wl_name)
-    orc, samp, frac, nq, _ = oracle_sample(wl_name, wl, cloud, target_s=1.0)
-    for _ in range(args.warmup):
-        oracle_step(orc, samp, wl)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        nq = oracle_step(orc, samp, wl)
-        times.append(time.perf_counter() - t0)
+    cores = host_cores()
+    with cf.ThreadPoolExecutor(max_workers=cores) as pool:
+        orc, parts, frac, nq, _ = oracle_sample_parallel(wl, cloud, pool, cores, target_s=1.0)
+        for _ in range(args.warmup):
+            oracle_step_parts(orc, parts, wl, pool)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            nq = oracle_step_parts(orc, parts, wl, pool)
+            times.append(time.perf_counter() - t0)
     T = sum(times)
     v = nq * args.steps / T
     line = {
         "impl": "reference", "metric": "ion-queries/s (exact kNN+RDF)", "value": v, "unit": "ion-queries/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample": f"z-slab with {frac:.3f} of the height (+2 nm halo)"},
-        "cpu_baseline": {"value": v, "unit": "ion-queries/s", "cores": 1, "kind": "oracle",
-                         "sample": f"z-slab {frac:.3f} of the needle height, {nq} centrals per step"},
+        "config": {"workload": wl["desc"], "sample": f"z-slab with {frac:.3f} of the height (+2 nm halo), "
+                                                        f"split in {cores} slabs of centrals, one host thread each"},
+        "cpu_baseline": {"value": v, "unit": "ion-queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"z-slab {frac:.3f} of the height in {cores} slabs (+2 nm halo each), "
+                                   f"{nq} centrals per step"},
         "e2e": {"value": v, "unit": "ion-queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -865,17 +921,32 @@ def run_gpu(args, wl_name, wl):
     # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        orc, samp, frac, nq, _ = oracle_sample(wl_name, wl, cloud, target_s=2.0)
-        reps = 0
-        t0 = time.perf_counter()
-        while reps < 3 or time.perf_counter() - t0 < 10.0:
+        import concurrent.futures as cf
+
+        # all host cores: independent oracle runs over consecutive z-slabs of centrals (exact sum)
+        cores = host_cores()
+        with cf.ThreadPoolExecutor(max_workers=cores) as pool:
+            orc, parts, frac, nq, _ = oracle_sample_parallel(wl, cloud, pool, cores, target_s=2.0)
+            reps = 0
+            t0 = time.perf_counter()
+            while reps < 3 or time.perf_counter() - t0 < 10.0:
+                oracle_step_parts(orc, parts, wl, pool)
+                reps += 1
+                if time.perf_counter() - t0 > 30.0:
+                    break
+            dt = time.perf_counter() - t0
+        # and one core, for reference
+        orc, samp, frac1, nq1, _ = oracle_sample(wl_name, wl, cloud, target_s=1.0)
+        t1 = time.perf_counter()
+        reps1 = 0
+        while reps1 < 2 or time.perf_counter() - t1 < 3.0:
             oracle_step(orc, samp, wl)
-            reps += 1
-            if time.perf_counter() - t0 > 30.0:
-                break
-        dt = time.perf_counter() - t0
-        cpu = {"value": nq * reps / dt, "unit": "ion-queries/s", "cores": 1, "kind": "oracle",
-               "sample": f"z-slab with {frac:.3f} of the height (+2 nm halo), {nq} centrals, {reps} runs"}
+            reps1 += 1
+        dt1 = time.perf_counter() - t1
+        cpu = {"value": nq * reps / dt, "unit": "ion-queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"z-slab with {frac:.3f} of the height split in {cores} slabs of centrals (+2 nm halo "
+                         f"each), one host thread each; {nq} centrals, {reps} runs",
+               "value_1core": nq1 * reps1 / dt1}
 
     if rank == 0:
         line = {
