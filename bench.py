@@ -689,8 +689,8 @@ def run_gpu(args, wl_name, wl):
     if len(wl["combos"]) > 1 and not args.serial_combos:
         combo_streams = [torch.cuda.Stream(device=dev) for _ in wl["combos"]]
 
-    def step(Xs=X, Ts=T, Ds=D):
-        if combo_streams is None:
+    def step(Xs=X, Ts=T, Ds=D, serial=False):
+        if combo_streams is None or serial:
             for (name, ctr, nbr), g, o in zip(wl["combos"], grids, outs):
                 g.build(Xs, Ts, nbr, r_cut)
                 ps.spatstat(g, Ds, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
@@ -734,10 +734,11 @@ def run_gpu(args, wl_name, wl):
     # dominant kernel family and its per-launch time: an eager pass with CUDA
     # events around every launch of the library (not the graph-timed region)
     fams = ["reset", "select", "geometry", "count", "scan", "scatter", "central", "query", "epilogue"]
+    # (the combinations one after the other on one stream, so that every launch is timed alone)
     ps.prof_enable(fams)
     for _ in range(args.steps):
         flush.zero_()
-        step()
+        step(serial=True)
     torch.cuda.synchronize()
     prof = {f: ps.prof_read(f) for f in fams}
     ps.prof_enable([])
@@ -890,7 +891,7 @@ def run_gpu(args, wl_name, wl):
     kcfg = {name: {"cell_scale": float(tuned[name]["cell_scale"]), "dense_min": int(tuned[name]["dense_min"])}
             for name, _, _ in wl["combos"]}
     common = {"kernel": dom, "peak_source": peak_kind, "avg_launch_us": avg_ms * 1e3, "launches": dom_n,
-              "timing": "CUDA events around each launch, eager pass",
+              "timing": "CUDA events around each launch, eager pass of the step with the combinations one after the other",
               "time_share": shares[dom] / max(1e-12, sum(shares.values())),
               "shares": {k: round(v / max(1e-12, sum(shares.values())), 4) for k, v in shares.items()}}
     hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
