@@ -44,3 +44,25 @@ def test_stored_traffic_guard():
 def test_alu_peak():
     peak, mhz = bench.alu_peak_tflops()
     assert peak == pytest.approx(152 * 128 * mhz * 1e6 / 1e12)
+
+
+@pytest.mark.parametrize("parts", [1, 3, 7])
+def test_slab_parts_sum_exactly(orc, parts):
+    """The all-core oracle baseline: independent oracle runs over consecutive z-slabs of centrals
+    (each with an r_cut halo of neighbours) add up to the oracle over the whole slab, histogram for
+    histogram (the halo holds every neighbour within r_cut of a slab's centrals)."""
+    rng = np.random.default_rng(11)
+    n = 6000
+    xyz = (rng.random((n, 3)) * np.array([6.0, 6.0, 14.0])).astype(np.float32)
+    t = rng.integers(0, 3, n).astype(np.uint8)
+    d = (rng.random(n) * 2.0).astype(np.float32)
+    r0, dr, nb = 0.0, 0.05, 20  # stop = 1.0 = the halo
+    ks = [1, 3]
+    whole = bench.slab_parts(xyz, t, d, 0.6, dr * nb, 1)[0]
+    ref = orc.spatstat(*whole, "all", [0, 2], 0.5, r0, dr, nb, ks)
+    got = [orc.spatstat(*p, "all", [0, 2], 0.5, r0, dr, nb, ks) for p in bench.slab_parts(xyz, t, d, 0.6, dr * nb, parts)]
+    assert ref["n_central"] > 0
+    assert sum(g["n_central"] for g in got) == ref["n_central"]
+    np.testing.assert_array_equal(sum(g["rdf"] for g in got), ref["rdf"])
+    np.testing.assert_array_equal(sum(g["knn"] for g in got), ref["knn"])
+    np.testing.assert_array_equal(sum(np.asarray(g["not_found"]) for g in got), np.asarray(ref["not_found"]))
