@@ -345,7 +345,8 @@ PS_API int ps_shuffle_labels(const uint8_t* type_in, uint8_t* type_out, int64_t 
  *     called.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address; make that first call before any stream capture.
- *   - n > PS_STATIC_MAX_IONS returns PS_ERR_CAPACITY with nothing enqueued.
+ *   - n > PS_STATIC_MAX_IONS returns PS_ERR_CAPACITY, n < 0 PS_ERR_INVALID_ARG,
+ *     with nothing enqueued.
  *   - Every call on a device shares the one array, which keeps the last call's
  *     contents (each call clears what must start at zero).  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race and give

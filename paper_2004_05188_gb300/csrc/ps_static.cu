@@ -67,7 +67,8 @@ extern "C" int ps_spatstat_static(const float* xyz, const uint8_t* type, const f
                                   const uint64_t nbr_mask[4], float r_cut, const uint64_t ctr_mask[4], float dsrf_min,
                                   ps_bins bins, const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn,
                                   uint64_t* d_meta, float* d_kth, uint32_t* d_nwithin, void* stream) {
-  if (n < 0 || n > (int64_t)PS_STATIC_MAX_IONS)
+  if (n < 0) return fail(PS_ERR_INVALID_ARG, "ps_spatstat_static: n < 0");
+  if (n > (int64_t)PS_STATIC_MAX_IONS)
     return fail(PS_ERR_CAPACITY, "ps_spatstat_static: n exceeds PS_STATIC_MAX_IONS (262144); use ps_build_grid");
   int dev = 0;
   PS_CUDA(cudaGetDevice(&dev));
