@@ -334,19 +334,20 @@ PS_API int ps_shuffle_labels(const uint8_t* type_in, uint8_t* type_out, int64_t 
 
 /*
  * Allocation-free ps_build_grid + ps_spatstat.  The paper has no counterpart:
- * this entry point exists for callers that may not allocate device memory
- * while they run the statistics, e.g. code running under CUDA stream capture
- * (the runtime refuses allocations inside a capture) or acquisition loops that
- * reserve all device memory up front and cannot afford the device-wide
- * synchronisation of cudaMalloc/cudaFree.
+ * this entry point exists for callers that cannot allocate device memory while
+ * they run the statistics, e.g. applications that give all device memory to
+ * their own pool at start-up (a cudaMalloc inside the library would fail) or
+ * acquisition loops that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree.
  *   - Scratch is one file-scope device array sized for PS_STATIC_MAX_IONS
  *     ions (about 14 MB), held on every GPU that uses the library until the
  *     process exits.  No cudaMalloc, cudaFree or other allocating routine is
  *     called.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address; make that first call before any stream capture.
- *   - n > PS_STATIC_MAX_IONS returns PS_ERR_CAPACITY, n < 0 PS_ERR_INVALID_ARG,
- *     with nothing enqueued.
+ *   - n > PS_STATIC_MAX_IONS returns PS_ERR_CAPACITY, n < 0 PS_ERR_INVALID_ARG;
+ *     every argument check of ps_grid_build and ps_spatstat is made before any
+ *     work is enqueued, so a refused call leaves the scratch untouched.
  *   - Every call on a device shares the one array, which keeps the last call's
  *     contents (each call clears what must start at zero).  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race and give

@@ -41,6 +41,27 @@ static int check_bins(ps_bins b) {
   return PS_OK;
 }
 
+
+// Host-side checks of the statistics arguments (everything ps_spatstat refuses before it
+// enqueues work), against the cutoff r_cut of the grid the query will search.
+int check_spatstat_args(const char* who, const uint64_t* ctr_mask, float dsrf_min, ps_bins bins, const uint32_t* ks,
+                        uint32_t n_k, const uint64_t* d_knn, const uint64_t* d_meta, float r_cut) {
+  const std::string w(who);
+  if (!ctr_mask || !d_meta) return fail(PS_ERR_INVALID_ARG, w + ": ctr_mask/d_meta is NULL");
+  int rc = check_bins(bins);
+  if (rc) return rc;
+  if (n_k > PS_MAX_KLIST) return fail(PS_ERR_UNSUPPORTED, w + ": too many k values");
+  if (n_k > 0 && (!ks || !d_knn)) return fail(PS_ERR_INVALID_ARG, w + ": ks/d_knn is NULL");
+  for (uint32_t q = 0; q < n_k; ++q)
+    if (ks[q] < 1 || ks[q] > PS_K_MAX) return fail(PS_ERR_UNSUPPORTED, w + ": k must be in [1, 32]");
+  if (std::isnan(dsrf_min)) return fail(PS_ERR_INVALID_ARG, w + ": dsrf_min is NaN");
+  // the largest edge, by the same formula as every kernel: E[n_bins] = (float)((r0 + n_bins dr)^2)
+  const double e = bins.r0 + (double)bins.n_bins * bins.dr;
+  const float Emax = (float)(e * e);
+  if ((double)Emax > (double)r_cut * (double)r_cut)
+    return fail(PS_ERR_INVALID_ARG, w + ": the grid's r_cut is below the histogram stop");
+  return PS_OK;
+}
 }  // namespace ps
 
 using namespace ps;
@@ -215,25 +236,8 @@ int ps_spatstat(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float
                 const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
                 uint32_t* d_nwithin, void* stream) {
   if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: grid is NULL or not built");
-  if (!ctr_mask || !d_meta) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: ctr_mask/d_meta is NULL");
-  int rc = check_bins(bins);
+  int rc = check_spatstat_args("ps_spatstat", ctr_mask, dsrf_min, bins, ks, n_k, d_knn, d_meta, g->r_cut);
   if (rc) return rc;
-  if (n_k > PS_MAX_KLIST) return fail(PS_ERR_UNSUPPORTED, "ps_spatstat: too many k values");
-  if (n_k > 0 && (!ks || !d_knn)) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: ks/d_knn is NULL");
-  for (uint32_t q = 0; q < n_k; ++q)
-    if (ks[q] < 1 || ks[q] > PS_K_MAX) return fail(PS_ERR_UNSUPPORTED, "ps_spatstat: k must be in [1, 32]");
-  if (std::isnan(dsrf_min)) return fail(PS_ERR_INVALID_ARG, "ps_spatstat: dsrf_min is NaN");
-  float Emax;
-  {
-    ps_bins one = bins;
-    float* E = new (std::nothrow) float[bins.n_bins + 1];
-    if (!E) return fail(PS_ERR_OOM, "host allocation failed");
-    edges_host(one, E);
-    Emax = E[bins.n_bins];
-    delete[] E;
-  }
-  if ((double)Emax > (double)g->r_cut * (double)g->r_cut)
-    return fail(PS_ERR_INVALID_ARG, "ps_spatstat: the grid's r_cut is below the histogram stop");
   return run_query(g, dsrf, ctr_mask, dsrf_min, bins, ks, n_k, d_rdf, d_knn, d_meta, d_kth, d_nwithin,
                    static_cast<cudaStream_t>(stream));
 }

@@ -191,6 +191,8 @@ __host__ __device__ inline float key2f(int32_t k) {
 }
 
 // host-side builders shared between translation units
+int check_spatstat_args(const char* who, const uint64_t* ctr_mask, float dsrf_min, ps_bins bins, const uint32_t* ks,
+                        uint32_t n_k, const uint64_t* d_knn, const uint64_t* d_meta, float r_cut);
 int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cudaStream_t s);
 // output arrays a central-list reset also zeroes (null pointers are skipped)
 struct ZeroOut {

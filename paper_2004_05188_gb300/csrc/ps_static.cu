@@ -1,15 +1,15 @@
 // Allocation-free exact kNN + RDF: the grid scratch lives in a file-scope
 // device array instead of memory from cudaMalloc.
 //
-// Who needs this: callers that may not allocate device memory when they run
-// the statistics, for example code that runs while its stream is being
-// captured into a CUDA graph (an allocation inside the capture is refused by
-// the runtime), and long-running acquisition or visualisation loops that
-// reserve all device memory at start-up and must not block on the implicit
-// device synchronisation of cudaMalloc/cudaFree in the loop.
+// Who needs this: callers that cannot allocate device memory when they run the
+// statistics, for example applications that hand all device memory to their
+// own pool at start-up (so a cudaMalloc inside the library would fail), and
+// long-running acquisition or visualisation loops that must not block on the
+// device-wide synchronisation that cudaMalloc/cudaFree imply.
 //
 // The array is sized for PS_STATIC_MAX_IONS ions (about 14 MB) and every
 // process that loads libps holds it on each GPU it uses until exit.
+#include <cmath>
 #include <mutex>
 
 #include "ps_internal.cuh"
@@ -70,6 +70,13 @@ extern "C" int ps_spatstat_static(const float* xyz, const uint8_t* type, const f
   if (n < 0) return fail(PS_ERR_INVALID_ARG, "ps_spatstat_static: n < 0");
   if (n > (int64_t)PS_STATIC_MAX_IONS)
     return fail(PS_ERR_CAPACITY, "ps_spatstat_static: n exceeds PS_STATIC_MAX_IONS (262144); use ps_build_grid");
+  // every argument check of the build and of the statistics comes first: a refused call
+  // enqueues nothing and leaves the shared scratch as it was
+  if (n > 0 && (!xyz || !type)) return fail(PS_ERR_INVALID_ARG, "ps_spatstat_static: xyz/type is NULL");
+  if (!nbr_mask) return fail(PS_ERR_INVALID_ARG, "ps_spatstat_static: nbr_mask is NULL");
+  if (!(r_cut > 0.0f) || !std::isfinite(r_cut)) return fail(PS_ERR_INVALID_ARG, "ps_spatstat_static: r_cut must be > 0");
+  int rc = check_spatstat_args("ps_spatstat_static", ctr_mask, dsrf_min, bins, ks, n_k, d_knn, d_meta, r_cut);
+  if (rc) return rc;
   int dev = 0;
   PS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(PS_ERR_UNSUPPORTED, "ps_spatstat_static: device index too large");
@@ -116,7 +123,7 @@ extern "C" int ps_spatstat_static(const float* xyz, const uint8_t* type, const f
   g.scan_ctr = reinterpret_cast<uint32_t*>(b + o_sctr);
   // The build kernels clear every counter and geometry field before use, so the
   // previous call's contents never leak into this one.
-  int rc = ps_grid_build(&g, xyz, type, n, nbr_mask, r_cut, stream);
+  rc = ps_grid_build(&g, xyz, type, n, nbr_mask, r_cut, stream);
   if (rc) return rc;
   return ps_spatstat(&g, dsrf, ctr_mask, dsrf_min, bins, ks, n_k, d_rdf, d_knn, d_meta, d_kth, d_nwithin, stream);
 }

@@ -76,3 +76,27 @@ def test_static_entry_point_sizes(L):
     args = (m, 2.0, m, 0.0, b, None, 0, None, None, None, None, None, None)
     _check(L, L.ps_spatstat_static(None, None, None, 262145, *args), CAPACITY, ["PS_STATIC_MAX_IONS"])
     _check(L, L.ps_spatstat_static(None, None, None, -1, *args), INVALID_ARG, ["n < 0"])
+
+
+def test_static_entry_point_checks_before_any_work(L):
+    """Every argument check of the allocation-free call comes before it enqueues anything (it
+    shares one scratch array, which a refused call must leave untouched): these fail here, on a
+    machine without a GPU, with the statistics' own messages."""
+    m = _mask(1)
+    meta = (ctypes.c_uint64 * 6)()
+    ks = (ctypes.c_uint32 * 1)(1)
+    good = ps.Bins(0.0, 0.01, 200)
+    _check(L, L.ps_spatstat_static(None, None, None, 0, m, 2.0, m, 0.0, ps.Bins(0.0, 0.01, 0), None, 0, None, None,
+                                   meta, None, None, None), UNSUPPORTED, ["n_bins"])
+    _check(L, L.ps_spatstat_static(None, None, None, 0, m, 2.0, m, 0.0, good, None, 0, None, None, None, None, None,
+                                   None), INVALID_ARG, ["ps_spatstat_static", "d_meta"])
+    _check(L, L.ps_spatstat_static(None, None, None, 0, m, 1.5, m, 0.0, good, None, 0, None, None, meta, None, None,
+                                   None), INVALID_ARG, ["r_cut is below the histogram stop"])
+    _check(L, L.ps_spatstat_static(None, None, None, 0, m, 2.0, m, 0.0, good, ks, 1, None, None, meta, None, None,
+                                   None), INVALID_ARG, ["ks/d_knn"])
+    _check(L, L.ps_spatstat_static(None, None, None, 0, m, 2.0, m, float("nan"), good, None, 0, None, None, meta, None,
+                                   None, None), INVALID_ARG, ["dsrf_min is NaN"])
+    _check(L, L.ps_spatstat_static(None, None, None, 5, m, 2.0, m, 0.0, good, None, 0, None, None, meta, None, None,
+                                   None), INVALID_ARG, ["xyz/type is NULL"])
+    _check(L, L.ps_spatstat_static(None, None, None, 0, None, 2.0, m, 0.0, good, None, 0, None, None, meta, None, None,
+                                   None), INVALID_ARG, ["nbr_mask is NULL"])

@@ -1,7 +1,8 @@
 """The allocation-free entry point ps_spatstat_static, through the C ABI.
 
-It serves callers that may not allocate device memory while they run (code
-under CUDA stream capture, loops that reserve all device memory up front).
+It serves callers that cannot allocate device memory while they run
+(applications that give all device memory to their own pool at start-up, loops
+that must not block on the device-wide synchronisation of cudaMalloc/cudaFree).
 Its output must equal that of the allocating path (ps_build_grid +
 ps_spatstat) bit for bit, on consecutive calls that share its static scratch.
 This file is collected last so that a failure here leaves every other test run.
