@@ -15,9 +15,10 @@ passage; voxelised displacements within the ROI radius R, Results on strong
 scaling) bins the float32 displacement of every in-range pair.  Maximum-separation
 clustering (same Methods passage: DBScan with d_max and N_min) labels the
 connected components of the d_max graph.
-The smoothed-RDF functions are FP64.  Parity for the g(r) normalisation
-constants is unpinned (the paper gives no formula); everything else is
-pinned by the tests under tests/test_oracle_*.py.
+The smoothed-RDF functions are FP64.  The g(r) normalisation (FP64) follows a
+reading, since the paper gives no formula; it is pinned by the uniform-density
+limit g -> 1 of a Poisson process and by the lattice's shell counts.  Every
+function is pinned by the tests under tests/test_oracle_*.py.
 """
 from __future__ import annotations
 
@@ -76,6 +77,8 @@ def _load():
         lib.orc_label_perm.restype = None
         lib.orc_shuffle_labels.argtypes = [P, P, i64, ctypes.c_uint64]
         lib.orc_shuffle_labels.restype = ctypes.c_int
+        lib.orc_rdf_normalise.argtypes = [P, u32, f64, f64, ctypes.c_uint64, ctypes.c_uint64, f64, P]
+        lib.orc_rdf_normalise.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -232,3 +235,14 @@ def shuffle_labels(type_, seed: int) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle shuffle_labels failed: {rc}")
     return out
+
+
+def rdf_normalise(rdf, r0: float, dr: float, n_central: int, n_nbr: int, volume: float) -> np.ndarray:
+    """g_b = H[b] / (n_central * (n_nbr / volume) * 4/3 pi (e_{b+1}^3 - e_b^3)), FP64 (orc_rdf_normalise)."""
+    h = np.ascontiguousarray(rdf, np.uint64)
+    g = np.empty(h.shape[0], np.float64)
+    rc = _load().orc_rdf_normalise(_ptr(h), h.shape[0], float(r0), float(dr), int(n_central), int(n_nbr),
+                                   float(volume), _ptr(g))
+    if rc:
+        raise ValueError(f"orc_rdf_normalise failed: {rc}")
+    return g

@@ -248,6 +248,30 @@ done:
   return rc;
 }
 
+/*
+ * Normalised RDF g(r) from the integer histogram (a derived output; the
+ * paper names the RDF as the distribution of neighbours in radial shells
+ * about every central ion, Methods "Descriptive, two-point spatial
+ * statistics, and clustering", and gives no normalisation).  Reading: the
+ * counts of bin b are divided by what a uniform neighbour density would put
+ * in that shell about every central:
+ *   g_b = H[b] / (n_central * rho * V_b),  rho = n_nbr / volume,
+ *   V_b = 4/3 pi (e_{b+1}^3 - e_b^3),  e_b = r0 + b dr   (double).
+ * n_central = 0 or n_nbr = 0 gives g = 0.  FP64.
+ */
+int orc_rdf_normalise(const uint64_t* rdf, uint32_t n_bins, double r0, double dr, uint64_t n_central,
+                      uint64_t n_nbr, double volume, double* g) {
+  if (n_bins == 0 || !(dr > 0) || !(r0 >= 0) || !(volume > 0)) return ORC_ERR_ARG;
+  const double rho = (double)n_nbr / volume;
+  for (uint32_t b = 0; b < n_bins; ++b) {
+    const double e0 = r0 + (double)b * dr, e1 = r0 + (double)(b + 1) * dr;
+    const double shell = 4.0 / 3.0 * M_PI * (e1 * e1 * e1 - e0 * e0 * e0);
+    const double expected = (double)n_central * rho * shell;
+    g[b] = expected > 0.0 ? (double)rdf[b] / expected : 0.0;
+  }
+  return ORC_OK;
+}
+
 /* Same contract as orc_spatstat, by O(N^2) brute force (no spatial index). */
 int orc_spatstat_brute(const float* xyz, const uint8_t* type, const float* dsrf, int64_t n, const uint64_t* ctr_mask,
                        const uint64_t* nbr_mask, float dsrf_min, double r0, double dr, uint32_t n_bins,
