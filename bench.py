@@ -376,15 +376,15 @@ def measure_soft(args, dev):
     rc = ps.soft_r_cut(bins, sigma, 1.0)
     g = ps.Grid(N)
     gp = ps.Grid(N)
-    # normalisation at fixed density: g_b = h_b / (N_c rho V_b)
+    # normalisation at fixed density (the library's g(r) finalisation, ps_rdf_normalise):
+    # g_b = h_b * factor_b, factor_b = 1 / (N_c (N / V) 4/3 pi (e_{b+1}^3 - e_b^3))
     vol = specimen.frustum_volume(p.r_top, math.degrees(p.half_angle), p.height)
-    e = np.arange(bins[2] + 1) * bins[1]
-    shell = torch.tensor(4.0 / 3.0 * np.pi * (e[1:] ** 3 - e[:-1] ** 3), dtype=torch.float32, device=dev)
-    rho = N / vol
     gp.build(Xp, T, "all", rc)
     h_star = ps.soft_rdf_fwd(gp, D, "all", dmin, sigma, 1.0, bins)
-    n_c = float(ps.spatstat(g.build(X, T, "all", rc), D, "all", dmin, bins, [], rdf=True)["meta"][0].item())
-    g_star = h_star / (n_c * rho * shell)
+    meta0 = ps.spatstat(g.build(X, T, "all", rc), D, "all", dmin, bins, [], rdf=True)["meta"]
+    n_c = float(meta0[0].item())
+    factor = ps.rdf_normalise(g, meta0, bins, vol)[1].float()
+    g_star = h_star * factor
     plain_out = dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
                      meta=torch.empty(ps.META_HEAD, dtype=torch.int64, device=dev))
 
@@ -393,8 +393,7 @@ def measure_soft(args, dev):
         return ps.soft_rdf_fwd(g, D, "all", dmin, sigma, 1.0, bins)
 
     def loss_grad(h):
-        gg = h / (n_c * rho * shell)
-        return 2.0 * (gg - g_star) / (n_c * rho * shell)
+        return 2.0 * (h * factor - g_star) * factor
 
     def bwd(G):
         return ps.soft_rdf_bwd(g, D, "all", dmin, sigma, 1.0, bins, G)

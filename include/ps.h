@@ -180,6 +180,29 @@ PS_API int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4]
                 uint64_t* d_hist, uint64_t* d_meta, void* stream);
 
 /*
+ * Normalised RDF g(r) from the integer histogram (the finalisation step).  The
+ * paper reports RDFs normalised (Methods, "Descriptive, two-point spatial
+ * statistics, and clustering") without a formula; the reading used here
+ * divides each bin by the count a uniform neighbour density rho = |N| / volume
+ * puts in that shell about each central:
+ *   g_b = H[b] / (|C| * rho * 4/3 pi (e_{b+1}^3 - e_b^3)),  e_b = r0 + b*dr,
+ * in FP64 (|C| = 0 or |N| = 0 gives 0).
+ *   g        the grid the histogram was computed on, not rebuilt since: |N| is
+ *            its neighbour count, read on the device
+ *   d_meta   device uint64 meta array of that ps_spatstat / ps_rdf_hist call
+ *            (|C| = d_meta[PS_META_N_CENTRAL])
+ *   d_rdf    device uint64 [n_bins], the histogram (may be NULL when d_g is)
+ *   volume   specimen volume in nm^3 (> 0), the same units as the coordinates
+ *   d_g      device double [n_bins] or NULL: g_b
+ *   d_factor device double [n_bins] or NULL: 1 / (|C| rho 4/3 pi (e_{b+1}^3 -
+ *            e_b^3)), the factor that turns counts (or a smoothed histogram)
+ *            into g
+ * At least one of d_g and d_factor is required.  Asynchronous on `stream`.
+ */
+PS_API int ps_rdf_normalise(ps_grid* g, const uint64_t* d_meta, const uint64_t* d_rdf, double volume, ps_bins bins,
+                            double* d_g, double* d_factor, void* stream);
+
+/*
  * Batched sweeps over many ROIs in one persistent launch.  The paper's batch
  * queue evaluates an a-priori list of (statistic, type combination, dataset)
  * tasks from one neighbour search per ROI (Suppl. "Customized user defined
@@ -388,7 +411,8 @@ typedef enum {
   PS_KID_LABELS = 13,    /* randomised labels */
   PS_KID_SDM = 14,       /* spatial distribution map */
   PS_KID_CLUSTER = 15,   /* maximum-separation clustering */
-  PS_KID_COUNT_ = 16
+  PS_KID_FINALISE = 16,  /* g(r) normalisation */
+  PS_KID_COUNT_ = 17
 } ps_kernel_id;
 PS_API uint64_t ps_launch_count(void);
 PS_API int ps_prof_enable(uint32_t kid_mask);

@@ -138,6 +138,7 @@ def lib():
     L.ps_sdm.argtypes = [P, P, P, f32, SdmSpec, P, P, P]
     L.ps_cluster.argtypes = [P, P, ClusterSpec, P, P, P, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
+    L.ps_rdf_normalise.argtypes = [P, P, P, ctypes.c_double, Bins, P, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
     L.ps_prof_read.argtypes = [u32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
@@ -151,7 +152,7 @@ def _check(rc: int):
 
 
 KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
-           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15)
+           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15, finalise=16)
 
 
 def launch_count() -> int:
@@ -296,6 +297,23 @@ def spatstat(grid: Grid, dsrf, ctr_types, dsrf_min: float, bins, ks=(), rdf: boo
         if st != 0:
             raise PSError(st, "device-side error reported in the meta status word")
     return out
+
+
+def rdf_normalise(grid: Grid, meta, bins, volume: float, rdf=None, stream=None):
+    """Normalised RDF (ps_rdf_normalise) of a histogram computed on `grid` (not rebuilt since).
+
+    meta: the int64 meta tensor of that spatstat call; volume: specimen volume (nm^3).
+    Returns (g, factor): float64 CUDA tensors [n_bins]; g is None when rdf is None.
+    factor_b = 1 / (|C| (|N| / volume) 4/3 pi (e_{b+1}^3 - e_b^3)), so g = rdf * factor."""
+    import torch
+
+    r0, dr, nb = bins
+    dev = grid._refs[0].device
+    f = torch.empty(nb, dtype=torch.float64, device=dev)
+    g = torch.empty(nb, dtype=torch.float64, device=dev) if rdf is not None else None
+    _check(lib().ps_rdf_normalise(grid.handle, _ptr(meta), _ptr(rdf), float(volume), Bins(r0, dr, nb), _ptr(g),
+                                  _ptr(f), _stream(stream)))
+    return g, f
 
 
 def knn_hist(grid: Grid, dsrf, ctr_types, dsrf_min: float, k: int, bins, stream=None):

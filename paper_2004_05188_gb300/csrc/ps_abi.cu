@@ -297,6 +297,18 @@ int ps_rdf_soft_bwd(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], f
                        static_cast<cudaStream_t>(stream));
 }
 
+int ps_rdf_normalise(ps_grid* g, const uint64_t* d_meta, const uint64_t* d_rdf, double volume, ps_bins bins,
+                     double* d_g, double* d_factor, void* stream) {
+  if (!g || !g->built) return fail(PS_ERR_INVALID_ARG, "ps_rdf_normalise: grid is NULL or not built");
+  if (!d_meta) return fail(PS_ERR_INVALID_ARG, "ps_rdf_normalise: d_meta is NULL");
+  if (!d_g && !d_factor) return fail(PS_ERR_INVALID_ARG, "ps_rdf_normalise: d_g and d_factor are both NULL");
+  if (d_g && !d_rdf) return fail(PS_ERR_INVALID_ARG, "ps_rdf_normalise: d_g needs d_rdf");
+  if (!(volume > 0.0) || !std::isfinite(volume)) return fail(PS_ERR_INVALID_ARG, "ps_rdf_normalise: volume must be > 0");
+  int rc = check_bins(bins);
+  if (rc) return rc;
+  return rdf_normalise(g, d_meta, d_rdf, volume, bins, d_g, d_factor, static_cast<cudaStream_t>(stream));
+}
+
 int ps_knn_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, uint32_t k, ps_bins bins,
                 uint64_t* d_hist, uint64_t* d_meta, float* d_kth, void* stream) {
   if (!d_hist) return fail(PS_ERR_INVALID_ARG, "ps_knn_hist: d_hist is NULL");

@@ -208,6 +208,8 @@ int run_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsr
             uint64_t* d_hist, uint64_t* d_meta, cudaStream_t s);
 int run_cluster(ps_grid* g, const float* dsrf, ps_cluster_spec spec, uint32_t* d_label, uint64_t* d_size_hist,
                 uint64_t* d_interior_hist, uint64_t* d_meta, cudaStream_t s);
+int rdf_normalise(ps_grid* gr, const uint64_t* d_meta, const uint64_t* d_rdf, double volume, ps_bins bins,
+                  double* d_g, double* d_factor, cudaStream_t s);
 int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                   ps_bins bins, const float* d_G, float* d_grad, float* d_grad_s, cudaStream_t s);
 

@@ -100,3 +100,8 @@ def test_static_entry_point_checks_before_any_work(L):
                                    None), INVALID_ARG, ["xyz/type is NULL"])
     _check(L, L.ps_spatstat_static(None, None, None, 0, None, 2.0, m, 0.0, good, None, 0, None, None, meta, None, None,
                                    None), INVALID_ARG, ["nbr_mask is NULL"])
+
+
+def test_rdf_normalise_arguments(L):
+    b = ps.Bins(0.0, 0.01, 200)
+    _check(L, L.ps_rdf_normalise(None, None, None, 1.0, b, None, None, None), INVALID_ARG, ["grid is NULL"])
