@@ -412,9 +412,55 @@ typedef enum {
   PS_KID_SDM = 14,       /* spatial distribution map */
   PS_KID_CLUSTER = 15,   /* maximum-separation clustering */
   PS_KID_FINALISE = 16,  /* g(r) normalisation */
-  PS_KID_COUNT_ = 17
+  PS_KID_PEAKS = 17,     /* throughput microbenchmarks (ps_measure_peaks) */
+  PS_KID_COUNT_ = 18
 } ps_kernel_id;
 PS_API uint64_t ps_launch_count(void);
+
+/*
+ * Measured throughput of the units the statistics are bound by (no
+ * counterpart in the paper): the denominators of the query's rooflines on the
+ * GPU at hand.  Runs three short microbenchmarks on `stream` (a few ms each,
+ * best of three) and synchronises; allocates and frees a few KB.
+ *   fp32_scalar_gops  1e9 float32 add/multiply results per second with scalar
+ *                     instructions (no fused multiply-add: the pair test is
+ *                     ((dx*dx)+(dy*dy))+(dz*dz), never contracted)
+ *   fp32_packed_gops  the same with packed f32x2 instructions
+ *   smem_atomic_gops  1e9 32-bit shared-memory atomic adds per second, every
+ *                     lane on its own bank (the conflict-free rate)
+ *   sm_mhz            SM clock during the runs (clock64 ticks per ns)
+ *   num_sms           multiprocessors of the current device
+ * out->struct_size must be sizeof(ps_peaks).
+ */
+typedef struct {
+  uint32_t struct_size;
+  int32_t num_sms;
+  double fp32_scalar_gops;
+  double fp32_packed_gops;
+  double smem_atomic_gops;
+  double sm_mhz;
+} ps_peaks;
+PS_API int ps_measure_peaks(ps_peaks* out, void* stream);
+
+/*
+ * Failure detection hooks for tests (no counterpart in the paper; the library's
+ * own convention that every failure returns a status and leaks nothing).
+ *   ps_debug_fail_alloc   the nth device allocation of the library from now on
+ *                         fails as if the device were out of memory (1 = the
+ *                         next one; 0 disarms).  The failing call must return
+ *                         PS_ERR_OOM and free whatever it had allocated.
+ *   ps_debug_live_allocs  device allocations of the library not yet freed.
+ *   ps_debug_wait_selftest  runs the library's two bounded device waits -- the
+ *                         look-back of the single-pass scans and the mbarrier
+ *                         wait of the bulk copies -- on events that never
+ *                         happen, each giving up after limit_ns (<= 2 s).
+ *                         d_work: device uint64 [4], overwritten; afterwards
+ *                         d_work[2] (look-back) and d_work[3] (mbarrier) hold
+ *                         PS_ERR_TIMEOUT.  Nothing is left in flight.
+ */
+PS_API int ps_debug_fail_alloc(int64_t nth);
+PS_API int64_t ps_debug_live_allocs(void);
+PS_API int ps_debug_wait_selftest(uint64_t limit_ns, uint64_t* d_work, void* stream);
 PS_API int ps_prof_enable(uint32_t kid_mask);
 PS_API int ps_prof_read(uint32_t kid, uint64_t* launches, double* total_ms);
 

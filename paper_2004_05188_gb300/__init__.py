@@ -97,6 +97,12 @@ class Sweep(ctypes.Structure):
                 ("nbr_mask", (ctypes.c_uint64 * 4) * 4), ("k_max", ctypes.c_uint32), ("cell_scale", ctypes.c_float)]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("num_sms", ctypes.c_int32), ("fp32_scalar_gops", ctypes.c_double),
+                ("fp32_packed_gops", ctypes.c_double), ("smem_atomic_gops", ctypes.c_double),
+                ("sm_mhz", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -139,6 +145,10 @@ def lib():
     L.ps_cluster.argtypes = [P, P, ClusterSpec, P, P, P, P, P]
     L.ps_spatstat_static.argtypes = [P, P, P, i64, P, f32, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_rdf_normalise.argtypes = [P, P, P, ctypes.c_double, Bins, P, P, P]
+    L.ps_measure_peaks.argtypes = [ctypes.POINTER(Peaks), P]
+    L.ps_debug_fail_alloc.argtypes = [i64]
+    L.ps_debug_live_allocs.restype = i64
+    L.ps_debug_wait_selftest.argtypes = [ctypes.c_uint64, P, P]
     L.ps_launch_count.restype = ctypes.c_uint64
     L.ps_prof_enable.argtypes = [u32]
     L.ps_prof_read.argtypes = [u32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
@@ -152,7 +162,17 @@ def _check(rc: int):
 
 
 KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
-           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15, finalise=16)
+           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15, finalise=16, peaks=17)
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured FP32 add/multiply, shared-atomic throughput and SM clock of the current GPU
+    (ps_measure_peaks; synchronises)."""
+    p = Peaks()
+    p.struct_size = ctypes.sizeof(Peaks)
+    _check(lib().ps_measure_peaks(ctypes.byref(p), _stream(stream)))
+    return dict(num_sms=p.num_sms, fp32_scalar_gops=p.fp32_scalar_gops, fp32_packed_gops=p.fp32_packed_gops,
+                smem_atomic_gops=p.smem_atomic_gops, sm_mhz=p.sm_mhz)
 
 
 def launch_count() -> int:

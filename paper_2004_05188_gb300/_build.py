@@ -21,7 +21,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # Translation units whose float32 arithmetic must not be contracted into FMA:
 # the exact path compares squared distances bit for bit, and ptxas fuses packed
 # (f32x2) multiplies and adds even when they carry an explicit rounding modifier.
-NO_FMA = {"ps_query.cu", "ps_grid.cu", "ps_batch.cu", "ps_sdm.cu", "ps_cluster.cu"}
+NO_FMA = {"ps_query.cu", "ps_grid.cu", "ps_batch.cu", "ps_sdm.cu", "ps_cluster.cu", "ps_peaks.cu", "ps_finalise.cu"}
 
 
 def _sources():

@@ -1,4 +1,5 @@
 // C ABI entry points of libps: argument checks, handle lifetime, dispatch.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -20,6 +21,31 @@ int cuda_fail(cudaError_t e, const char* what) {
   t_error = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA;
 }
+
+// Every device allocation of the library goes through dev_malloc / dev_free: they keep the
+// count of live allocations and host the failure injection of ps_debug_fail_alloc.
+static std::atomic<int64_t> g_fail_countdown{0};
+static std::atomic<int64_t> g_live_allocs{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  int64_t c = g_fail_countdown.load();
+  while (c > 0 && !g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 1) return cudaErrorMemoryAllocation;  // the injected failure: nothing is allocated
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  const cudaError_t e = cudaFree(p);
+  if (e == cudaSuccess) g_live_allocs.fetch_sub(1);
+  return e;
+}
+
+int wait_selftest(uint64_t limit_ns, unsigned long long* d_work, cudaStream_t s);
 
 int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
               const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
@@ -108,12 +134,6 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   g->cell_cap = (uint32_t)(cap < (int64_t)1 << 31 ? cap : (int64_t)1 << 31);
   // scan tiles of 4096 cells or 4096 records (the central list's record compaction)
   g->scan_tiles_cap = (uint32_t)(((int64_t)g->cell_cap > g->n_max + 1 ? (int64_t)g->cell_cap : g->n_max + 1) + 4095) / 4096;
-  cudaError_t e = cudaGetDevice(&g->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
-  if (e != cudaSuccess) {
-    delete g;
-    return cuda_fail(e, "cudaGetDevice");
-  }
   const size_t nm = (size_t)g->n_max, cc = g->cell_cap;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -131,10 +151,17 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   const size_t o_part = take((size_t)g->scan_tiles_cap * 8), o_sctr = take(8);
   const size_t o_ngeo = take(sizeof(Geo)), o_cgeo = take(sizeof(Geo));
   void* base = nullptr;
-  e = cudaMalloc(&base, off);
+  cudaError_t e = dev_malloc(&base, off);
   if (e != cudaSuccess) {
     delete g;
     return cuda_fail(e, "cudaMalloc(grid scratch)");
+  }
+  e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e != cudaSuccess) {
+    dev_free(base);
+    delete g;
+    return cuda_fail(e, "cudaGetDevice");
   }
   char* b = static_cast<char*>(base);
   g->dev_block = base;
@@ -163,7 +190,7 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   if (e == cudaSuccess) e = cudaMemset(g->scan_ctr, 0, 8);
   if (e == cudaSuccess) e = cudaMemset(g->ctr.geo, 0, sizeof(Geo));
   if (e != cudaSuccess) {
-    cudaFree(base);
+    dev_free(base);
     delete g;
     return cuda_fail(e, "cudaMemset(grid)");
   }
@@ -176,7 +203,7 @@ int ps_grid_destroy(ps_grid* g) {
   cudaError_t e = cudaSuccess;
   if (g->dev_block) {
     e = cudaDeviceSynchronize();
-    cudaError_t e2 = cudaFree(g->dev_block);
+    cudaError_t e2 = dev_free(g->dev_block);
     if (e == cudaSuccess) e = e2;
   }
   delete g;
@@ -320,6 +347,20 @@ int ps_rdf_hist(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float
   if (!d_hist) return fail(PS_ERR_INVALID_ARG, "ps_rdf_hist: d_hist is NULL");
   return ps_spatstat(g, dsrf, ctr_mask, dsrf_min, bins, nullptr, 0, d_hist, nullptr, d_meta, nullptr, nullptr,
                      stream);
+}
+
+int ps_debug_fail_alloc(int64_t nth) {
+  if (nth < 0) return fail(PS_ERR_INVALID_ARG, "ps_debug_fail_alloc: nth < 0");
+  g_fail_countdown.store(nth);
+  return PS_OK;
+}
+
+int64_t ps_debug_live_allocs(void) { return g_live_allocs.load(); }
+
+int ps_debug_wait_selftest(uint64_t limit_ns, uint64_t* d_work, void* stream) {
+  if (!d_work) return fail(PS_ERR_INVALID_ARG, "ps_debug_wait_selftest: d_work is NULL");
+  if (limit_ns > kWaitLimitNs) return fail(PS_ERR_INVALID_ARG, "ps_debug_wait_selftest: limit_ns above 2 s");
+  return wait_selftest(limit_ns, reinterpret_cast<unsigned long long*>(d_work), static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

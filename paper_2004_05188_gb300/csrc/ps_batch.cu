@@ -498,20 +498,20 @@ int ps_batch_create(const ps_dataset* ds, int n_ds, const ps_sweep* sw, ps_batch
   }
   auto cleanup = [&](int code) {
     for (ps_grid* g : b->grids) ps_grid_destroy(g);
-    cudaFree(b->d_roi);
-    cudaFree(b->d_item_off);
-    cudaFree(b->d_next);
-    cudaFree(b->d_rbins);
-    cudaFree(b->d_acc);
+    dev_free(b->d_roi);
+    dev_free(b->d_item_off);
+    dev_free(b->d_next);
+    dev_free(b->d_rbins);
+    dev_free(b->d_acc);
     delete b;
     return code;
   };
   if (rc) return cleanup(rc);
-  cudaError_t e = cudaMalloc(&b->d_roi, sizeof(BRoi) * n_ds);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_item_off, sizeof(uint32_t) * (n_ds + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_rbins, sizeof(uint32_t) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_acc, sizeof(unsigned long long) * (size_t)b->acc_len * n_ds);
+  cudaError_t e = dev_malloc((void**)&b->d_roi, sizeof(BRoi) * n_ds);
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_item_off, sizeof(uint32_t) * (n_ds + 1));
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_next, sizeof(uint32_t));
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_rbins, sizeof(uint32_t) * 4);
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_acc, sizeof(unsigned long long) * (size_t)b->acc_len * n_ds);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(batch)"));
   std::vector<BRoi> h(n_ds);
   for (int i = 0; i < n_ds; ++i) {
@@ -530,11 +530,11 @@ int ps_batch_destroy(ps_batch* b) {
   if (!b) return PS_OK;
   cudaDeviceSynchronize();
   for (ps_grid* g : b->grids) ps_grid_destroy(g);
-  cudaFree(b->d_roi);
-  cudaFree(b->d_item_off);
-  cudaFree(b->d_next);
-  cudaFree(b->d_rbins);
-  cudaFree(b->d_acc);
+  dev_free(b->d_roi);
+  dev_free(b->d_item_off);
+  dev_free(b->d_next);
+  dev_free(b->d_rbins);
+  dev_free(b->d_acc);
   delete b;
   return PS_OK;
 }

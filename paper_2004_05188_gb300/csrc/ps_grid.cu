@@ -434,8 +434,9 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 // at a time (lane l reads tile j - l; the window is summed up to the nearest tile
 // that holds an inclusive prefix; the virtual tile -1 holds prefix 0), publishes
 // the inclusive prefix and returns the exclusive one in every lane.  A wait on a
-// predecessor gives up after kWaitLimitNs and records PS_ERR_TIMEOUT in *status.
-__device__ uint32_t tile_lookback(uint32_t t, uint32_t total, unsigned long long* state, int* status) {
+// predecessor gives up after limit_ns and records PS_ERR_TIMEOUT in *status.
+__device__ uint32_t tile_lookback(uint32_t t, uint32_t total, unsigned long long* state, int* status,
+                                  uint64_t limit_ns = kWaitLimitNs) {
   const uint32_t lane = lane_id();
   uint32_t prefix = 0;
   if (t > 0) {
@@ -453,7 +454,7 @@ __device__ uint32_t tile_lookback(uint32_t t, uint32_t total, unsigned long long
         int give_up = 0;
         if (lane == 0) {
           if (t0 == 0) t0 = global_ns();
-          give_up = global_ns() - t0 > kWaitLimitNs;
+          give_up = global_ns() - t0 > limit_ns;
         }
         if (__shfl_sync(0xffffffffu, give_up, 0)) {
           if (lane == 0) atomicCAS(status, 0, (int)PS_ERR_TIMEOUT);
@@ -728,6 +729,35 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const float* __restrict__ 
     const uint32_t w = type ? ((i << 8) | type[i]) : i;
     rec[start[c.x] + c.y] = make_float4(xyz[b], xyz[b + 1], xyz[b + 2], __uint_as_float(w));
   }
+}
+
+// Self-test of the two bounded waits of the library on events that never happen
+// (one warp): the look-back of a scan tile whose predecessor never publishes, and
+// an mbarrier phase that nothing completes.  Each must give up after limit_ns and
+// report PS_ERR_TIMEOUT; nothing is in flight when the kernel returns.
+//   work[0], work[1]  look-back words of tiles 0 and 1 (tile 0 stays unpublished)
+//   work[2]           status of the look-back wait (low 32 bits)
+//   work[3]           status of the mbarrier wait
+__global__ void k_wait_selftest(unsigned long long* work, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    work[0] = 0ull;
+    work[1] = 0ull;
+    work[2] = 0ull;
+    work[3] = 0ull;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __threadfence();
+  __syncwarp();
+  tile_lookback(1, 0, work, reinterpret_cast<int*>(work + 2), limit_ns);
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_ns)) work[3] = (unsigned long long)PS_ERR_TIMEOUT;
+}
+
+int wait_selftest(uint64_t limit_ns, unsigned long long* d_work, cudaStream_t s) {
+  PS_LAUNCH(PS_KID_SCAN, s, k_wait_selftest<<<1, 32, 0, s>>>(d_work, limit_ns));
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
 }
 
 static int grid_blocks(const ps_grid* g, int per_sm) { return g->num_sms * per_sm; }

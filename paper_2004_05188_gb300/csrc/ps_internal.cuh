@@ -19,6 +19,10 @@ void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// device allocations of the library (live count, failure injection)
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+
 void prof_begin(uint32_t kid, cudaStream_t s);
 void prof_end(uint32_t kid, cudaStream_t s);
 // every kernel launch of the library goes through this (launch count + optional event timing)

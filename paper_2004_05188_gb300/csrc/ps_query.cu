@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
   const Geo ng = *a.ngeo;
   const uint32_t work_n = a.cgeo->work_n;
   const uint32_t n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
-  uint32_t phase = 0;
+  uint32_t phase = 0, stuck_phase = 0;
   uint64_t my_binned = 0, my_below = 0;
 
   for (;;) {
@@ -685,6 +685,7 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
         r = rr;
         ro = rro;
         if (!mbar_wait_bounded(&bar, phase, kWaitLimitNs)) s_timeout = 1;
+        const uint32_t this_phase = phase;
         phase ^= 1u;
 
         if (valid) {
@@ -702,7 +703,12 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
           }
         }
         __syncthreads();  // the chunk buffer is reused next
+        if (s_timeout) {  // uniform after the barrier: issue no more copies
+          stuck_phase = this_phase;
+          break;
+        }
       }
+      if (s_timeout) break;
       if (valid) {
         if (a.nwithin) a.nwithin[pidx] = within;
         if (KMAX > 0)
@@ -710,6 +716,12 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
       }
     }
     __syncthreads();  // s_item and the run table are rewritten next
+  }
+  if (s_timeout) {
+    // the copies of the phase that timed out may still be in flight into this CTA's shared
+    // memory: wait for them once more (bounded) before the CTA exits
+    if (tid == 0) mbar_wait_bounded(&bar, stuck_phase, kWaitLimitNs);
+    __syncthreads();
   }
   H.flush(a);
   add_pair_counters(a, my_binned, my_below);
