@@ -1,21 +1,33 @@
 #!/usr/bin/env python
-"""Benchmark of the exact kNN + RDF spatial-statistics path on one GB300.
+"""Benchmark of the exact kNN + RDF spatial-statistics path on GB300.
 
-Default workload: the ~8.07e6-ion needle (tip radius 20 nm, half-angle
-10 deg, height 100 nm, 30 ions/nm^3, Al3Sc precipitates), type combinations
-Sc-Sc and Si-Si, k in {1, 5, 10}, RDF on r = [0, 0.01, 2] nm, central ions
-with d_srf >= 2 nm.  One step = for each combination: build the neighbour
-cell grid (binner) and run the kNN + RDF query (central list + query
-kernel), i.e. every step of the exact path, with inputs resident in HBM.
+Default workload: the full-scale needle of 2e9 ions (tip radius 40 nm,
+half-angle 15 deg, height 812.6 nm, 30 ions/nm^3, Al3Sc precipitates), type
+combinations all-all and Sc-Sc, k = 10, RDF on r = [0, 0.01, 2] nm, central
+ions with d_srf >= 2 nm.  One step = for each combination: build the
+neighbour cell grid (binner) and run the kNN + RDF query (central list +
+query kernel), i.e. every step of the exact path, with inputs resident in
+HBM.  With N ranks the specimen is cut into N z-slabs of equal ion count
+(each rank generates and holds only its slab plus an r_cut halo) and the
+integer results are summed with one all-reduce per combination: strong
+scaling of one specimen.
 
-value   = ion queries (central ions evaluated, summed over the combinations
-          and over ranks) per second of device time.
+value   = ion queries (central ions evaluated, summed over the combinations)
+          per second of device time, max over ranks.
 e2e     = the same metric through the public Python API with the inputs in
           pinned host memory: H2D copy + both combinations + D2H of results.
-roofline: the dominant kernel family, timed with CUDA events on its stream
-          in the timed region, against the measured HBM copy bandwidth.
-cpu_baseline: the oracle (C) on a bounded z-slab sample, on every host core (one
-          z-slab of centrals per thread, exact sum), and on one core.
+roofline: the query kernel (the dominant family), timed with CUDA events
+          around every launch on its stream inside the timed region, against
+          the FP32 add/multiply throughput measured on the GPU at hand; beside
+          it the shared-atomic bound of its RDF increments and the HBM
+          fraction of the build kernels.
+cpu_baseline: the oracle (C) on a bounded z-slab sample of the same needle,
+          on every host core (one share of the sample's centrals per thread,
+          exact sum).
+secondary: the 8.07e6-ion needle (Sc-Sc + Si-Si, k = 1, 5, 10) and the
+          2e5-ion cylinder (all-all), each step replayed from a CUDA graph.
+forms:  the smoothed RDF (1e7 needle), the batched sweep (256 ROIs), the
+          spatial distribution map and the clustering sweep (8e6 needle).
 
 --impl reference runs the oracle as the comparison arm on the host cores.
 """
@@ -38,19 +50,21 @@ sys.path.insert(0, ROOT)
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 WORKLOADS = {
+    "needle2g": dict(
+        desc="needle 2e9 ions (r_tip 40 nm, 15 deg, h 812.6 nm, 30/nm^3, Al3Sc precipitates); all-all + Sc-Sc; "
+             "kNN k=10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
+        combos=[("all-all", "all", "all"), ("Sc-Sc", [1], [1])], ks=[10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0,
+        sharded=True),
     "needle8m": dict(
         desc="needle 8.07e6 ions (r_tip 20 nm, 10 deg, h 100 nm, 30/nm^3, Al3Sc precipitates); Sc-Sc + Si-Si; "
              "kNN k=1,5,10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
         combos=[("Sc-Sc", [1], [1]), ("Si-Si", [2], [2])], ks=[1, 5, 10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
-    "needle2g": dict(
-        desc="needle 2e9 ions (r_tip 40 nm, 15 deg, h 812.6 nm, 30/nm^3, Al3Sc precipitates); all-all + Sc-Sc; "
-             "kNN k=10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
-        combos=[("all-all", "all", "all"), ("Sc-Sc", [1], [1])], ks=[10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
     "cylinder200k": dict(
         desc="Poisson cylinder 2e5 ions (R 10 nm, H 15.9 nm, 40/nm^3); all-all; kNN k=1 + RDF r=[0,0.01,2] nm; "
              "d_srf>=1 nm",
         combos=[("all-all", "all", "all")], ks=[1], spec=(0.0, 0.01, 2.0), dsrf_min=1.0),
 }
+SECONDARY = ("needle8m", "cylinder200k")
 
 
 def make_cloud(name: str, seed_offset: int = 0):
@@ -60,33 +74,28 @@ def make_cloud(name: str, seed_offset: int = 0):
         return specimen.needle(specimen.needle_8m_params(seed=2 + seed_offset))
     if name == "cylinder200k":
         return specimen.cylinder_small(seed=1 + seed_offset)
-    if name == "needle2g":
-        return specimen.needle(specimen.needle_2g_params(seed=5 + seed_offset))
     raise ValueError(name)
 
 
-def load_peaks():
+def needle_params(name: str):
+    from paper_2004_05188_gb300 import specimen
+
+    if name == "needle2g":
+        return specimen.needle_2g_params()
+    raise ValueError(name)
+
+
+def load_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json, STREAM-style copy)"
     return 6800.0, "fallback"
 
 
-# FP32 pipe: 152 SMs x 128 lanes, one non-fused FP32 operation per lane per clock
-N_SM, FP32_LANES = 152, 128
-FLOPS_PER_CANDIDATE = 9  # d2 = ((dx*dx) + (dy*dy)) + (dz*dz): 3 sub, 3 mul, 2 add; 1 compare against the range
-
-
-def alu_peak_tflops():
-    """FP32 (non-FMA) peak from the unit counts and the maximum SM clock."""
-    mhz = 2070.0
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", mhz))
-    return N_SM * FP32_LANES * mhz * 1e6 / 1e12, mhz
+# the pair test d2 = ((dx*dx) + (dy*dy)) + (dz*dz): 3 sub, 3 mul, 2 add, and 1 compare against the range
+FLOPS_PER_CANDIDATE = 9
 
 
 def query_sources_sha256() -> str:
@@ -100,26 +109,28 @@ def query_sources_sha256() -> str:
     return h.hexdigest()
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_traffic.json")
+
+
 def stored_traffic(workload: str, kernel_config: dict):
-    """DRAM bytes per query launch from the committed ncu summary, or None when that summary was
-    taken on other kernel sources, another workload or another kernel configuration."""
-    p = os.path.join(ROOT, "profiles", "query_traffic_needle8m.md")
-    if not os.path.exists(p):
+    """DRAM bytes per query launch from the stored ncu record (profiles/query_traffic.json), or None
+    when no record was taken on these kernel sources, this workload and this kernel configuration."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    with open(p) as f:
-        for line in f:
-            if line.startswith("record: "):
-                rec = json.loads(line[len("record: "):])
-                if (rec.get("workload") == workload and rec.get("source_sha256") == query_sources_sha256()
-                        and rec.get("kernel_config") == kernel_config):
-                    return float(rec["dram_bytes_per_launch"])
+    with open(TRAFFIC_FILE) as f:
+        recs = json.load(f).get("records", [])
+    for rec in recs:
+        if (rec.get("workload") == workload and rec.get("source_sha256") == query_sources_sha256()
+                and rec.get("kernel_config") == kernel_config):
+            return float(rec["dram_bytes_per_launch"])
     return None
 
 
-def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil):
+def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26):
     """Central x candidate tests one query makes on this grid: for every central, the neighbour
     records in the (2*stencil+1)^3 cells around its cell (clipped at the grid's faces).
-    Counted with plain torch ops from the grid geometry (reporting only, untimed)."""
+    Counted with plain torch ops from the grid geometry (reporting only, untimed), in chunks of
+    ions so that the temporaries stay small beside a 2e9-ion cloud."""
     import torch
 
     import paper_2004_05188_gb300 as ps
@@ -131,6 +142,7 @@ def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil):
     dims = info["dims"]
     org = torch.tensor(info["origin"], dtype=torch.float32, device=X.device)
     inv_h = float(np.float32(1.0 / float(info["cell"])))
+    ln, lc = lut(nbr), lut(ctr)
 
     def cells(P):
         u = torch.floor((P - org) * inv_h).to(torch.int64)
@@ -138,19 +150,25 @@ def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil):
             u[:, a].clamp_(0, dims[a] - 1)
         return (u[:, 2] * dims[1] + u[:, 1]) * dims[0] + u[:, 0]
 
-    Tl = T.long()
-    cnt = torch.bincount(cells(X[lut(nbr)[Tl]]), minlength=info["n_cells"]).view(dims[2], dims[1], dims[0])
+    n = X.shape[0]
+    cnt = torch.zeros(info["n_cells"], dtype=torch.int64, device=X.device)
+    for a in range(0, n, chunk):
+        sel = ln[T[a:a + chunk].long()]
+        cnt += torch.bincount(cells(X[a:a + chunk][sel]), minlength=info["n_cells"])
+    cnt = cnt.view(dims[2], dims[1], dims[0])
     s = int(stencil)
     for ax in range(3):  # box sum of width 2s+1 along each axis (exact, int64)
         c = torch.cumsum(torch.nn.functional.pad(cnt.movedim(ax, -1), (s + 1, s)), dim=-1)
-        cnt = (c[..., 2 * s + 1:] - c[..., : -(2 * s + 1)]).movedim(-1, ax)
-    cm = lut(ctr)[Tl] & (D >= dsrf_min)
-    return int(cnt.reshape(-1)[cells(X[cm])].sum().item())
+        cnt = (c[..., 2 * s + 1:] - c[..., : -(2 * s + 1)]).movedim(-1, ax).contiguous()
+        del c
+    cnt = cnt.reshape(-1)
+    tot = 0
+    for a in range(0, n, chunk):
+        cm = lc[T[a:a + chunk].long()] & (D[a:a + chunk] >= dsrf_min)
+        tot += int(cnt[cells(X[a:a + chunk][cm])].sum().item())
+    return tot
 
 
-# ---------------------------------------------------------------------------
-# clocks sampling during the timed region
-# ---------------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -205,19 +223,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle arm (cpu baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def slab_sample(xyz, t, d, frac: float, halo: float):
-    """A z-slab holding `frac` of the z-extent: its ions plus a halo of neighbours; halo ions are not central."""
-    z = xyz[:, 2]
-    zlo, zhi = float(z.min()), float(z.max())
-    z0 = zlo + 0.5 * (zhi - zlo) * (1.0 - frac)
-    z1 = z0 + frac * (zhi - zlo)
-    keep = (z >= z0 - halo) & (z < z1 + halo)
-    core = (z >= z0) & (z < z1)
-    ds = np.where(core[keep], d[keep], np.float32(-1e30)).astype(np.float32)
-    return xyz[keep], t[keep], ds
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
 
 
-def oracle_step(orc, cloud, wl):
+def oracle_run(orc, cloud, wl):
+    """One oracle step over a cloud (every combination); returns the centrals evaluated."""
     xyz, t, d = cloud
     r0, dr, nb = wl["bins"]
     n = 0
@@ -227,130 +241,143 @@ def oracle_step(orc, cloud, wl):
     return n
 
 
-def host_cores() -> int:
-    try:
-        return max(1, len(os.sched_getaffinity(0)))
-    except AttributeError:
-        return max(1, os.cpu_count() or 1)
+def needle_sample(wl_name, wl, core_layers: int, shares: int):
+    """Bounded sample of the large needle for the oracle: `core_layers` lattice layers about the
+    middle of its height whose ions are the centrals, with the r_cut halo of neighbour layers on
+    each side, generated directly (the same ions as the full cloud's).  The centrals are split
+    into `shares` strips along x of equal count (one host thread each); a strip's cloud is every
+    ion of the slab within r_cut of the strip in x, so the strips add up exactly."""
+    from paper_2004_05188_gb300 import shard, specimen
+
+    p = needle_params(wl_name)
+    counts = specimen.needle_plan(p)
+    mid = len(counts) // 2
+    lo = mid - core_layers // 2
+    hi = lo + core_layers
+    r0, dr, nb = wl["bins"]
+    r_cut = r0 + dr * nb
+    halo = shard.halo_layers(p.a, r_cut, p.sig_z)
+    xyz, t, d, (i0, i1) = shard.slab_needle(p, counts, [lo, hi], 0, halo)
+    x = xyz[:, 0]
+    cx = np.sort(x[i0:i1])
+    cuts = [-np.inf] + [float(cx[len(cx) * j // shares]) for j in range(1, shares)] + [np.inf]
+    core = np.zeros(x.shape[0], bool)
+    core[i0:i1] = True
+    parts = []
+    for j in range(shares):
+        keep = (x >= cuts[j] - r_cut) & (x < cuts[j + 1] + r_cut)
+        own = core[keep] & (x[keep] >= cuts[j]) & (x[keep] < cuts[j + 1])
+        parts.append((xyz[keep], t[keep], np.where(own, d[keep], np.float32(np.nan)).astype(np.float32)))
+    desc = (f"{core_layers} lattice layers of centrals at mid-height ({i1 - i0} ions) + {halo}-layer halo each side "
+            f"({xyz.shape[0]} ions generated), centrals in {shares} strips along x with an r_cut halo each "
+            f"(one host thread each)")
+    return parts, desc
 
 
-def slab_parts(xyz, t, d, frac: float, halo: float, parts: int):
-    """The z-slab of slab_sample split into `parts` consecutive z-slabs of centrals, each with its own
-    halo of neighbours: independent oracle runs over them add up to the whole slab's exact counts."""
+def small_sample(wl, cloud, frac: float, shares: int):
+    """Bounded z-slab sample of a small cloud: the ions of a z-slab holding `frac` of the height are
+    the centrals' candidates, with an r_cut halo; their centrals split into `shares` index ranges."""
+    xyz, t, d = cloud
     z = xyz[:, 2]
     zlo, zhi = float(z.min()), float(z.max())
     z0 = zlo + 0.5 * (zhi - zlo) * (1.0 - frac)
     z1 = z0 + frac * (zhi - zlo)
-    cuts = [z0 + (z1 - z0) * i / parts for i in range(parts + 1)]
-    out = []
-    for a, b in zip(cuts[:-1], cuts[1:]):
-        keep = (z >= a - halo) & (z < b + halo)
-        core = (z >= a) & (z < b)
-        out.append((xyz[keep], t[keep], np.where(core[keep], d[keep], np.float32(-1e30)).astype(np.float32)))
-    return out
+    r0, dr, nb = wl["bins"]
+    halo = r0 + dr * nb
+    keep = (z >= z0 - halo) & (z < z1 + halo)
+    core = ((z >= z0) & (z < z1))[keep]
+    xs, ts, ds = xyz[keep], t[keep], np.where(core, d[keep], np.float32(np.nan)).astype(np.float32)
+    idx = np.nonzero(core)[0]
+    parts = []
+    for j in range(shares):
+        sel = idx[len(idx) * j // shares: len(idx) * (j + 1) // shares]
+        dj = np.full_like(ds, np.float32(np.nan))
+        dj[sel] = ds[sel]
+        parts.append((xs, ts, dj))
+    return parts, f"z-slab with {frac:.3f} of the height (+{halo} nm halo), centrals in {shares} shares"
 
 
-def oracle_step_parts(orc, parts, wl, pool):
-    """One step of the oracle on every part, one host thread each (ctypes releases the GIL; the
-    oracle keeps no global state)."""
-    return sum(pool.map(lambda c: oracle_step(orc, c, wl), parts))
+def oracle_sampled(wl_name, wl, cores: int, target_s: float, cloud=None):
+    """A sample sized so that one oracle step on `cores` threads takes about target_s."""
+    import concurrent.futures as cf
 
-
-def oracle_sample_parallel(wl, cloud, pool, cores: int, target_s=1.0):
-    """Bounded sample for the oracle on `cores` host threads: a z-slab, split in `cores` parts,
-    whose parallel run takes ~target_s."""
     import oracle as orc
 
     orc.build()
-    xyz, t, d = cloud
-    halo = wl["bins"][1] * wl["bins"][2]
-    frac = min(1.0, 0.02 * cores)
+    pool = cf.ThreadPoolExecutor(max_workers=cores)
+    size = 1 if wl.get("sharded") else 0.02
     while True:
-        parts = slab_parts(xyz, t, d, frac, halo, cores)
+        if wl.get("sharded"):
+            parts, desc = needle_sample(wl_name, wl, int(size), cores)
+        else:
+            parts, desc = small_sample(wl, cloud, float(size), cores)
         t0 = time.perf_counter()
-        nq = oracle_step_parts(orc, parts, wl, pool)
+        nq = sum(pool.map(lambda c: oracle_run(orc, c, wl), parts))
         dt = time.perf_counter() - t0
-        if dt >= 0.25 * target_s or frac >= 1.0:
+        full = size >= 1.0 if not wl.get("sharded") else False
+        if dt >= 0.3 * target_s or full:
             break
-        frac = min(1.0, frac * max(2.0, 0.5 * target_s / max(dt, 1e-3)))
-    return orc, parts, frac, nq, dt
+        grow = max(2.0, 0.6 * target_s / max(dt, 1e-3))
+        size = min(1.0, size * grow) if not wl.get("sharded") else max(size + 1, int(size * grow))
+    return orc, parts, pool, nq, desc
 
 
-def oracle_sample(wl_name, wl, cloud, target_s=1.0):
-    """Bounded sample of the workload for the oracle: a z-slab whose single-threaded run takes ~target_s."""
-    import oracle as orc
-
-    xyz, t, d = cloud
-    frac = 0.02
-    while True:
-        samp = slab_sample(xyz, t, d, frac, wl["bins"][1] * wl["bins"][2])
-        t0 = time.perf_counter()
-        nq = oracle_step(orc, samp, wl)
-        dt = time.perf_counter() - t0
-        if dt >= 0.25 * target_s or frac >= 1.0:
-            break
-        frac = min(1.0, frac * max(2.0, 0.5 * target_s / max(dt, 1e-3)))
-    return orc, samp, frac, nq, dt
+def oracle_steps(orc, parts, pool, wl, n):
+    """n oracle steps over the sample (one thread per share); returns (centrals per step, seconds)."""
+    t0 = time.perf_counter()
+    nq = 0
+    for _ in range(n):
+        nq = sum(pool.map(lambda c: oracle_run(orc, c, wl), parts))
+    return nq, time.perf_counter() - t0
 
 
 def run_reference(args, wl_name, wl):
-    import concurrent.futures as cf
-
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cloud = make_cloud(wl_name)
     cores = host_cores()
-    with cf.ThreadPoolExecutor(max_workers=cores) as pool:
-        orc, parts, frac, nq, _ = oracle_sample_parallel(wl, cloud, pool, cores, target_s=1.0)
-        for _ in range(args.warmup):
-            oracle_step_parts(orc, parts, wl, pool)
-        times = []
-        for _ in range(args.steps):
-            t0 = time.perf_counter()
-            nq = oracle_step_parts(orc, parts, wl, pool)
-            times.append(time.perf_counter() - t0)
-    T = sum(times)
+    cloud = None if wl.get("sharded") else make_cloud(wl_name)
+    orc, parts, pool, nq, desc = oracle_sampled(wl_name, wl, cores, target_s=2.0, cloud=cloud)
+    oracle_steps(orc, parts, pool, wl, args.warmup)
+    nq, T = oracle_steps(orc, parts, pool, wl, args.steps)
+    pool.shutdown()
     v = nq * args.steps / T
     line = {
         "impl": "reference", "metric": "ion-queries/s (exact kNN+RDF)", "value": v, "unit": "ion-queries/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample": f"z-slab with {frac:.3f} of the height (+2 nm halo), "
-                                                        f"split in {cores} slabs of centrals, one host thread each"},
+        "higher_is_better": True, "scaling": "strong" if wl.get("sharded") else "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": desc},
         "cpu_baseline": {"value": v, "unit": "ion-queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"z-slab {frac:.3f} of the height in {cores} slabs (+2 nm halo each), "
-                                   f"{nq} centrals per step"},
+                         "sample": f"{desc}; {nq} centrals per step"},
         "e2e": {"value": v, "unit": "ion-queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-# ---------------------------------------------------------------------------
-# the GPU arm
-# ---------------------------------------------------------------------------
-def algorithmic_bytes(kid: str, st: dict) -> float:
-    """Bytes the kernel family must move per step (reads + writes of its role), summed over the combinations."""
+def algorithmic_bytes(kid: str, st: dict, c: dict) -> float:
+    """Bytes one combination's kernels of a family must move per step (reads + writes of their role).
+    n: ions of the cloud, nn: neighbour-set ions, nc: centrals, cells: cells of the grid."""
     N = st["n_ions"]
-    tot = 0.0
-    for c in st["combos"]:
-        nn, nc, cells, ntm = c["n_nbr"], c["n_central"], c["n_cells"], c["n_ctr_typed"]
-        if kid == "select":
-            tot += N * 1 + nn * 12 + nn * 4
-        elif kid == "central":
-            tot += cells * 4 + N * 1 + ntm * 4 + nc * 12 + nc * 12
-        elif kid == "count":
-            tot += nn * (4 + 12 + 8)
-        elif kid == "scatter":
-            tot += nn * (4 + 8 + 12 + 4 + 16) + nc * (4 + 8 + 12 + 4 + 16)
-        elif kid == "scan":
-            tot += 2 * cells * (4 + 4 + 4 + 4)
-        elif kid == "geometry":
-            tot += cells * 4
-        elif kid == "query":
-            tot += nn * 16 + nc * 16 + 2 * cells * 4
-    return tot
+    nn, nc, cells, ntm = c["n_nbr"], c["n_central"], c["n_cells"], c["n_ctr_typed"]
+    if kid == "select":  # type labels of every ion; xyz of the selected; their indices written
+        return N * 1 + nn * 12 + nn * 4
+    if kid == "geometry":  # cell counts zeroed
+        return cells * 4
+    if kid == "count":  # index read, xyz gathered, count increment, (cell, rank) written
+        return nn * (4 + 12 + 4 + 8)
+    if kid == "scan":  # counts read, starts written; central-list cell starts from the record prefix
+        return cells * (4 + 4) + cells * (4 + 4 + 4)
+    if kid == "scatter":  # index, (cell, rank), start read; xyz gathered; float4 record written
+        return nn * (4 + 8 + 4 + 12 + 16)
+    if kid == "central":
+        if c.get("subset", True):  # records read, type and d_srf gathered, prefix and central records written
+            return nn * (16 + 1 + 4 + 4) + nc * 16
+        return N * 1 + ntm * 4 + nc * (12 + 4 + 8) + nc * (4 + 8 + 4 + 12 + 16)
+    if kid == "query":  # every record and central read once; cell starts
+        return nn * 16 + nc * 16 + 2 * cells * 4
+    return 0.0
 
 
 def measure_soft(args, dev):
@@ -533,9 +560,8 @@ def measure_cluster(args, dev):
 def measure_batched(args, dev):
     """256 ROIs (needles and cylinders, log-uniform 1e4..1e7 ions), each with the sweep
     k = 1..20, r_max in {1, 2, 3} nm (0.01 nm bins), d_srf >= {0, 1, 2} nm, type pairs
-    all-all, Sc-Sc, Al-Sc: one CUDA-graph replay of the batched path for all ROIs; and, on a
-    subset of 16 ROIs spread over the size range, the batched path against one plain exact
-    call per ROI and sweep point (27 calls per ROI, each with k = 1..20)."""
+    all-all, Sc-Sc, Al-Sc: one CUDA-graph replay of the batched path for all ROIs, against one
+    plain exact call per ROI and sweep point (27 calls per ROI, each with k = 1..20) on all ROIs."""
     import torch
 
     import paper_2004_05188_gb300 as ps
@@ -588,84 +614,294 @@ def measure_batched(args, dev):
     del out
 
     ks = list(range(1, k_max + 1))
-    grids = {i: ps.Grid(rois[i][0].shape[0], best_cs) for i in sub}
+    # the plain path on all ROIs: one grid build per (ROI, pair, r_max) and one ps_spatstat per sweep point
+    grid = ps.Grid(max(r[0].shape[0] for r in rois), best_cs)
+    pouts = {nb: dict(rdf=torch.empty(nb, dtype=torch.int64, device=dev),
+                      knn=torch.empty((k_max, nb), dtype=torch.int64, device=dev),
+                      meta=torch.empty(4 + 2 * k_max, dtype=torch.int64, device=dev)) for nb in rmax}
 
-    def plain_all():
-        for i in sub:
+    def plain(idx):
+        for i in idx:
             X, T, D = rois[i]
             for ctr, nbr in pairs:
                 for nb in rmax:
-                    grids[i].build(X, T, nbr, nb * 0.01 * (1 + 1e-6))
+                    grid.build(X, T, nbr, nb * 0.01 * (1 + 1e-6))
                     for dmin in dsrf:
-                        ps.spatstat(grids[i], D, ctr, dmin, (0.0, 0.01, nb), ks, check=False)
+                        ps.spatstat(grid, D, ctr, dmin, (0.0, 0.01, nb), ks, out=pouts[nb], check=False)
 
-    plain_all()
+    plain(sub)  # warm-up
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    plain_all()
+    plain(range(len(rois)))
     e1.record()
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1)
-    for gd in grids.values():
-        gd.close()
+    grid.close()
     return {"workload": f"{len(rois)} ROIs, {n_ions} ions (log-uniform 1e4..1e7), k=1..20, r_max {{1,2,3}} nm, "
                         "d_srf {0,1,2} nm, pairs all-all/Sc-Sc/Al-Sc",
-            "sweep_points": len(rois) * 27, "batched_ms": all_ms,
-            "ion_queries_per_s": n_central_all / (all_ms * 1e-3),
-            "subset_rois": len(sub), "subset_batched_ms": sub_ms, "subset_plain_ms": plain_ms,
-            "plain_over_batched": plain_ms / sub_ms, "cell_scale": best_cs,
+            "sweep_points": len(rois) * 27, "batched_ms": all_ms, "plain_ms": plain_ms,
+            "plain_over_batched": plain_ms / all_ms,
+            "ion_queries_per_s": n_central_all / (all_ms * 1e-3), "cell_scale": best_cs,
             "autotune_subset_ms": {f"cell_scale={k[0]}": round(v, 2) for k, v in sub_t.items()},
             "host_generation_s": gen_s,
-            "timing": "CUDA events; batched = one CUDA-graph replay (grid builds + one persistent query "
-                      "kernel + expansion); plain = one eager ps_spatstat per ROI and sweep point"}
+            "timing": "CUDA events; batched = one CUDA-graph replay for all ROIs (grid builds + one persistent "
+                      "query kernel + expansion); plain = one eager grid build per (ROI, pair, r_max) and one "
+                      "ps_spatstat per sweep point, all ROIs"}
 
 
-def rank_reduce(dist, device, t_max, sums):
-    """Whole-job numbers across ranks: the slowest rank's time and the summed counts.
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+FAMS = ["reset", "select", "geometry", "count", "scan", "scatter", "central", "query", "epilogue"]
+BUILD_FAMS = ("select", "geometry", "count", "scan", "scatter", "central")
 
-    dist is torch.distributed (or None for one process); device is where the reduction
-    tensors live (a CUDA device under NCCL, the CPU under gloo)."""
+
+def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
+    """Roofline figures of one measurement: the query against the measured FP32 add/multiply
+    throughput (its bound) and against the measured shared-atomic rate (its RDF increments), and
+    the build kernels against the measured HBM copy bandwidth.  prof: {family: (launches, ms)}
+    summed over `steps` steps; st: per-step counts of every combination."""
+    q_n, q_ms = prof["query"]
+    cands = sum(c["candidates"] for c in st["combos"]) * steps
+    pairs = sum(c["n_pairs_local"] for c in st["combos"]) * steps
+    alu_peak = max(peaks["fp32_scalar_gops"], peaks["fp32_packed_gops"]) * 1e-3  # TFLOP/s
+    alu = FLOPS_PER_CANDIDATE * cands / (q_ms * 1e-3) / 1e12 if q_ms > 0 else 0.0
+    atom_rate = pairs / (q_ms * 1e-3) / 1e9 if q_ms > 0 else 0.0
+    q_bytes = sum(algorithmic_bytes("query", st, c) for c in st["combos"]) * steps
+    b_bytes = sum(algorithmic_bytes(f, st, c) for f in BUILD_FAMS for c in st["combos"]) * steps
+    b_ms = sum(prof[f][1] for f in BUILD_FAMS)
+    tot_ms = sum(v[1] for v in prof.values())
+    return {
+        "bound": "alu", "kernel": "query (k_query_warp)", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+        "frac": alu / alu_peak if alu_peak > 0 else None,
+        "peak_source": f"measured: ps_measure_peaks FP32 add/multiply, {peaks['num_sms']} SMs at "
+                       f"{peaks['sm_mhz']:.0f} MHz (scalar {peaks['fp32_scalar_gops']:.0f}, packed f32x2 "
+                       f"{peaks['fp32_packed_gops']:.0f} Gop/s; the larger is the peak)",
+        "traffic": traffic, "traffic_note": "DRAM bytes per query launch, stored ncu record (profiles/query_traffic.json) "
+                                            "for these kernel sources and this configuration; null if none",
+        "per_unit": f"{FLOPS_PER_CANDIDATE} FP32 operations per candidate test (3 sub, 3 mul, 2 add, 1 compare)",
+        "candidate_tests_per_step": cands // max(1, steps), "flops_per_launch": FLOPS_PER_CANDIDATE * cands / max(1, q_n),
+        "launches": q_n, "avg_launch_ms": q_ms / max(1, q_n),
+        "timing": "CUDA events around every launch on the launching stream, inside the timed region",
+        "time_share": q_ms / tot_ms if tot_ms > 0 else None,
+        "shares": {k: round(v[1] / tot_ms, 5) for k, v in prof.items()} if tot_ms > 0 else None,
+        "smem_atomic": {"achieved": atom_rate, "peak": peaks["smem_atomic_gops"], "unit": "G shared-atomic adds/s",
+                        "frac": atom_rate / peaks["smem_atomic_gops"] if peaks["smem_atomic_gops"] > 0 else None,
+                        "per_unit": "one 32-bit shared-memory increment per neighbour pair binned",
+                        "peak_source": "measured: ps_measure_peaks, conflict-free 32-bit shared atomics"},
+        "hbm_query": {"achieved": q_bytes / (q_ms * 1e-3) / 1e9 if q_ms > 0 else 0.0, "peak": hbm_peak,
+                      "unit": "GB/s", "per_unit": "16 B per neighbour record + 16 B per central + 8 B per cell"},
+        "hbm_build": {"achieved": b_bytes / (b_ms * 1e-3) / 1e9 if b_ms > 0 else 0.0, "peak": hbm_peak,
+                      "unit": "GB/s", "frac": (b_bytes / (b_ms * 1e-3) / 1e9) / hbm_peak if b_ms > 0 else None,
+                      "kernels": list(BUILD_FAMS), "ms_per_step": b_ms / max(1, steps),
+                      "algorithmic_bytes_per_step": b_bytes / max(1, steps), "peak_source": hbm_src},
+    }
+
+
+def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil):
+    """Counts of one combination after its build + query (reporting only, untimed)."""
+    meta = o["meta"].cpu().numpy()
+    if meta[3] != 0:
+        raise RuntimeError(f"device status {meta[3]} for {name}")
+    info = g.info()
+    mc, mn = ps.type_mask(ctr), ps.type_mask(nbr)
+    lut = np.array([bool((int(mc[v >> 6]) >> (v & 63)) & 1) for v in range(256)])
+    n_typed = sum(int(np.count_nonzero(lut[t_host[a:a + (1 << 26)]])) for a in range(0, t_host.shape[0], 1 << 26))
+    return dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
+                n_ctr_typed=n_typed, n_pairs_local=int(meta[1]), subset=bool(np.all((mc & ~mn) == 0)),
+                candidates=candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil))
+
+
+def e2e_runner(dev, stream, sets, hosts, step, outs, res_h):
+    """End to end through the public API: every step copies its inputs from pinned host memory on a
+    copy stream (into one of the device buffer sets, so that the copy of step k+1 overlaps the
+    compute of step k when there are two sets), runs the step and reads the results back."""
     import torch
 
-    if dist is None:
-        return float(t_max), [float(x) for x in sums]
-    tt = torch.tensor([float(t_max)], dtype=torch.float64, device=device)
-    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    ss = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
-    dist.all_reduce(ss)
-    return float(tt.item()), [float(x) for x in ss.tolist()]
+    copy_s = torch.cuda.Stream(device=dev)
+    ev_copy = [torch.cuda.Event() for _ in sets]
+    ev_used = [torch.cuda.Event() for _ in sets]
+
+    def d2h():
+        for o, h in zip(outs, res_h):
+            for k in o:
+                if o[k] is not None:
+                    h[k].copy_(o[k], non_blocking=True)
+
+    def run(n_steps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        copy_s.wait_event(t0)
+        for k in range(n_steps):
+            b = k % len(sets)
+            with torch.cuda.stream(copy_s):
+                if k >= len(sets):
+                    copy_s.wait_event(ev_used[b])
+                for dst, src in zip(sets[b], hosts):
+                    dst.copy_(src, non_blocking=True)
+                ev_copy[b].record(copy_s)
+            stream.wait_event(ev_copy[b])
+            step(*sets[b])
+            ev_used[b].record(stream)
+            d2h()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    return run
 
 
-def run_gpu(args, wl_name, wl):
+def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
+    """The large needle, slab-sharded over the ranks (one slab at N = 1): eager steps with the
+    library's per-launch events on, inside the timed region."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+    from paper_2004_05188_gb300 import shard, specimen
+
+    bins = wl["bins"]
+    r_cut = float(np.float32(bins[0] + bins[1] * bins[2]))
+    p = needle_params(wl_name)
+    t0 = time.perf_counter()
+    counts = specimen.needle_plan(p)
+    cuts = shard.layer_cuts(counts, world)
+    halo = shard.halo_layers(p.a, r_cut, p.sig_z)
+    pinned = []
+
+    def alloc(n):
+        bufs = (torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
+                torch.empty(n, dtype=torch.uint8, pin_memory=True),
+                torch.empty(n, dtype=torch.float32, pin_memory=True))
+        pinned.extend(bufs)
+        return tuple(b.numpy() for b in bufs)
+
+    xyz, t, d, core = shard.slab_needle(p, counts, cuts, rank, halo, alloc)
+    gen_s = time.perf_counter() - t0
+    Xh, Th, Dh = pinned
+    N = xyz.shape[0]
+    X = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    T = torch.empty(N, dtype=torch.uint8, device=dev)
+    D = torch.empty(N, dtype=torch.float32, device=dev)
+    for dst, src in zip((X, T, D), (Xh, Th, Dh)):
+        dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+
+    # cell size for the grid shared by the combinations: the autotuner's choice for the dominant
+    # combination, timed on a contiguous z-slice of the local cloud (1/32 of it; untimed)
+    name0, ctr0, nbr0 = wl["combos"][0]
+    if args.no_autotune:
+        tuned = {"cell_scale": args.cell_scale, "dense_min": args.dense_min, "timings_ms": None}
+    else:
+        from paper_2004_05188_gb300 import autotune
+
+        a = N // 2 - N // 64
+        b = a + N // 32
+        tuned = autotune.tune(X[a:b], T[a:b], D[a:b], nbr0, ctr0, wl["dsrf_min"], bins, wl["ks"],
+                              candidates=((1.0, 0), (0.5, 0)), reps=2)
+    cs, dm = tuned["cell_scale"], tuned["dense_min"]
+    grid = ps.Grid(N, cs, dm)
+    nk = len(wl["ks"])
+    outs = [dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
+                 knn=torch.empty((nk, bins[2]), dtype=torch.int64, device=dev),
+                 meta=torch.empty(ps.META_HEAD + 2 * nk, dtype=torch.int64, device=dev)) for _ in wl["combos"]]
+    stream = torch.cuda.current_stream()
+
+    def step(Xs=X, Ts=T, Ds=D):
+        for (name, ctr, nbr), o in zip(wl["combos"], outs):
+            grid.build(Xs, Ts, nbr, r_cut)
+            ps.spatstat(grid, Ds, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
+        for o in outs:
+            shard.combine(dist, o)
+
+    # one verified pass per combination (device status, local counts for the rooflines)
+    st = {"n_ions": N, "combos": []}
+    stencil = 1 if cs >= 1.0 else 2
+    for (name, ctr, nbr), o in zip(wl["combos"], outs):
+        grid.build(X, T, nbr, r_cut)
+        ps.spatstat(grid, D, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
+        torch.cuda.synchronize()
+        st["combos"].append(combo_stats(ps, grid, o, name, ctr, nbr, X, T, D, t, wl, stencil))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_queries = sum(int(o["meta"][0].item()) for o in outs)  # every rank's centrals (after the combine)
+    n_pairs = sum(int(o["meta"][1].item()) for o in outs)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(gpu_index(local_rank()), args.clocks_csv)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ps.prof_enable(FAMS)
+    sampler.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    lc0 = ps.launch_count()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (not timed)
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    wall = time.perf_counter() - wall0
+    launches = ps.launch_count() - lc0
+    clocks = sampler.stop()
+    prof = {f: ps.prof_read(f) for f in FAMS}
+    ps.prof_enable([])
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    T_ms, _ = rank_reduce(dist, dev, float(sum(step_ms)), [])
+    value = n_queries * args.steps / (T_ms * 1e-3)
+
+    e2e = None
+    if not args.no_e2e:
+        res_h = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in outs]
+        sets = [(X, T, D)]
+        free = torch.cuda.mem_get_info(dev)[0]
+        if free > X.nbytes + T.nbytes + D.nbytes + (8 << 30):  # a second input set: copies overlap compute
+            sets.append((torch.empty_like(X), torch.empty_like(T), torch.empty_like(D)))
+        run = e2e_runner(dev, stream, sets, (Xh, Th, Dh), step, outs, res_h)
+        run(len(sets))
+        E_ms, _ = rank_reduce(dist, dev, run(args.steps), [])
+        h2d = Xh.nbytes + Th.nbytes + Dh.nbytes
+        d2h = sum(v.numel() * v.element_size() for o in outs for v in o.values())
+        e2e = {"value": n_queries * args.steps / (E_ms * 1e-3), "unit": "ion-queries/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": E_ms / args.steps, "steps": args.steps,
+               "mode": (f"{len(sets)} device input set(s): " +
+                        ("the H2D of step k+1 overlaps the compute of step k" if len(sets) > 1 else
+                         "H2D, compute and D2H in sequence"))}
+        del sets, res_h
+
+    hbm_peak, hbm_src = load_hbm_peak()
+    kcfg = {name: {"cell_scale": float(cs), "dense_min": int(dm)} for name, _, _ in wl["combos"]}
+    roof = rooflines(prof, st, args.steps, peaks, hbm_peak, hbm_src, stored_traffic(wl_name, kcfg))
+    grid.close()
+    res = {"value": value, "T_ms": T_ms, "n_queries": n_queries, "n_pairs": n_pairs, "launches": launches,
+           "clocks": clocks, "wall": wall, "e2e": e2e, "roofline": roof, "n_ions_local": N,
+           "kernel_config": kcfg, "autotune": tuned.get("timings_ms"), "generation_s": gen_s,
+           "slab": {"layers": [int(cuts[rank]), int(cuts[rank + 1])], "halo_layers": halo, "ions_generated": N,
+                    "core_ions": int(core[1] - core[0])},
+           "step_ms_min_max": [min(step_ms), max(step_ms)]}
+    del X, T, D, pinned, Xh, Th, Dh
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, steps, warmup, do_e2e):
+    """A small workload, one independent specimen per rank: each step captured once in a CUDA
+    graph and replayed; the per-launch timing comes from an eager pass with the library's
+    per-launch events (the combinations one after the other, so that every launch is timed alone)."""
     import torch
 
     import paper_2004_05188_gb300 as ps
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    dev = torch.device("cuda", local)
     cloud = make_cloud(wl_name, seed_offset=1000 * rank)
     xyz, t, d = cloud
     N = xyz.shape[0]
-    X = torch.from_numpy(xyz).to(dev)
-    T = torch.from_numpy(t).to(dev)
-    D = torch.from_numpy(d).to(dev)
+    X, T, D = (torch.from_numpy(a).to(dev) for a in (xyz, t, d))
     bins = wl["bins"]
     r_cut = float(np.float32(bins[0] + bins[1] * bins[2]))
-    # kernel configuration per combination: measured by the autotuner on this cloud (untimed)
     tuned = {}
     for name, ctr, nbr in wl["combos"]:
         if args.no_autotune:
@@ -673,19 +909,17 @@ def run_gpu(args, wl_name, wl):
         else:
             from paper_2004_05188_gb300 import autotune
 
-            tuned[name] = autotune.tune(X, T, D, nbr, ctr, wl["dsrf_min"], wl["bins"], wl["ks"])
+            tuned[name] = autotune.tune(X, T, D, nbr, ctr, wl["dsrf_min"], bins, wl["ks"])
     grids = [ps.Grid(N, tuned[name]["cell_scale"], tuned[name]["dense_min"]) for name, _, _ in wl["combos"]]
     nk = len(wl["ks"])
-    outs = []
-    for _ in wl["combos"]:
-        outs.append(dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
-                         knn=torch.empty((nk, bins[2]), dtype=torch.int64, device=dev),
-                         meta=torch.empty(ps.META_HEAD + 2 * nk, dtype=torch.int64, device=dev)))
+    outs = [dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
+                 knn=torch.empty((nk, bins[2]), dtype=torch.int64, device=dev),
+                 meta=torch.empty(ps.META_HEAD + 2 * nk, dtype=torch.int64, device=dev)) for _ in wl["combos"]]
     stream = torch.cuda.current_stream()
-    # the type combinations are independent analyses: each runs on its own stream, so that the
-    # short, latency-bound kernels of one overlap with the other's
     combo_streams = None
     if len(wl["combos"]) > 1 and not args.serial_combos:
+        # the type combinations are independent analyses: each on its own stream, so that the
+        # short, latency-bound kernels of one overlap with the other's
         combo_streams = [torch.cuda.Stream(device=dev) for _ in wl["combos"]]
 
     def step(Xs=X, Ts=T, Ds=D, serial=False):
@@ -705,210 +939,153 @@ def run_gpu(args, wl_name, wl):
             cur.wait_stream(cs)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    # correctness of the configuration before timing: device status words
     step()
     torch.cuda.synchronize()
     st = {"n_ions": N, "combos": []}
-    n_queries = 0
-    n_pairs = 0
     for (name, ctr, nbr), g, o in zip(wl["combos"], grids, outs):
-        meta = o["meta"].cpu().numpy()
-        if meta[3] != 0:
-            raise RuntimeError(f"device status {meta[3]} for {name}")
-        info = g.info()
-        ctr_set = range(256) if ctr == "all" else ctr
-        ntm = int(np.isin(t, list(ctr_set)).sum())
         stencil = 1 if tuned[name]["cell_scale"] >= 1.0 else 2
-        st["combos"].append(dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
-                                 n_ctr_typed=ntm, n_pairs=int(meta[1]),
-                                 candidates=candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil)))
-        n_queries += int(meta[0])
-        n_pairs += int(meta[1])
-
-    for _ in range(args.warmup):
+        st["combos"].append(combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t, wl, stencil))
+    n_queries = sum(c["n_central"] for c in st["combos"])
+    n_pairs = sum(c["n_pairs_local"] for c in st["combos"])
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-
-    # dominant kernel family and its per-launch time: an eager pass with CUDA
-    # events around every launch of the library (not the graph-timed region)
-    fams = ["reset", "select", "geometry", "count", "scan", "scatter", "central", "query", "epilogue"]
-    # (the combinations one after the other on one stream, so that every launch is timed alone)
-    ps.prof_enable(fams)
-    for _ in range(args.steps):
+    ps.prof_enable(FAMS)
+    for _ in range(steps):
         flush.zero_()
         step(serial=True)
     torch.cuda.synchronize()
-    prof = {f: ps.prof_read(f) for f in fams}
+    prof = {f: ps.prof_read(f) for f in FAMS}
     ps.prof_enable([])
-    shares = {f: v[1] for f, v in prof.items()}
-    dom = max(shares, key=shares.get)
-    dom_n, dom_ms = prof[dom]
-    eager_ms = None
-
-    # the timed step: the whole pass captured once in a CUDA graph, replayed per step
-    graph = None
-    kernels_per_step = None
-    if not args.no_graph:
-        lc = ps.launch_count()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        kernels_per_step = ps.launch_count() - lc
-        for _ in range(3):
-            graph.replay()
-        torch.cuda.synchronize()
-
-    def timed_step():
-        if graph is not None:
-            graph.replay()
-        else:
-            step()
-
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else
-                           int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]), args.clocks_csv)
-    sampler.start()
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
+    lc = ps.launch_count()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    kernels_per_step = ps.launch_count() - lc
+    for _ in range(3):
+        graph.replay()
     torch.cuda.synchronize()
-    lc0 = ps.launch_count()
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (not timed)
+    sampler = ClockSampler(gpu_index(local_rank()), None)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
         ev0[k].record(stream)
-        timed_step()
+        graph.replay()
         ev1[k].record(stream)
     torch.cuda.synchronize()
-    barrier()
-    wall = time.perf_counter() - wall0
-    launches = ps.launch_count() - lc0 if graph is None else kernels_per_step * args.steps
+    barrier(dist)
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    T_ms, (tot_q, tot_p) = rank_reduce(dist, dev, float(sum(step_ms)), [n_queries, n_pairs])
-    value = tot_q * args.steps / (T_ms * 1e-3)
-
-    # ---- e2e through the public API, inputs in pinned host memory ----
+    T_ms, (tot_q, tot_p) = rank_reduce(dist, dev, float(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))),
+                                       [n_queries, n_pairs])
     e2e = None
-    if not args.no_e2e:
-        Xh = torch.from_numpy(xyz).pin_memory()
-        Th = torch.from_numpy(t).pin_memory()
-        Dh = torch.from_numpy(d).pin_memory()
+    if do_e2e:
+        Xh, Th, Dh = (torch.from_numpy(a).pin_memory() for a in (xyz, t, d))
         res_h = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in outs]
-
-        def d2h():
-            for o, h in zip(outs, res_h):
-                for k in o:
-                    h[k].copy_(o[k], non_blocking=True)
-
-        if graph is not None:
-            # pipelined: every step copies its own inputs into one of two device buffer sets on a
-            # copy stream, overlapping the previous step's compute; the compute stream replays
-            # the graph captured for that buffer set and reads the results back.  No L2 flush:
-            # the 137 MB of inputs per step exceed the 129 MB L2.
-            XB, TB, DB = torch.empty_like(X), torch.empty_like(T), torch.empty_like(D)
-            graph_b = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph_b):
-                step(XB, TB, DB)
-            sets, graphs = [(X, T, D), (XB, TB, DB)], [graph, graph_b]
-            # the inputs are copied in n_cs contiguous slices on as many streams (several copy
-            # engines share the host link)
-            n_cs = args.copy_streams
-            copy_ss = [torch.cuda.Stream(device=dev) for _ in range(n_cs)]
-            ev_copy = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(2)]
-            ev_used = [torch.cuda.Event(), torch.cuda.Event()]
-
-            def slices(n):
-                cut = [n * i // n_cs for i in range(n_cs + 1)]
-                return [(cut[i], cut[i + 1]) for i in range(n_cs)]
-
-            def run_e2e(n_steps):
-                t0 = torch.cuda.Event(enable_timing=True)
-                t1 = torch.cuda.Event(enable_timing=True)
-                t0.record(stream)
-                for cs in copy_ss:
-                    cs.wait_event(t0)
-                for k in range(n_steps):
-                    b = k % 2
-                    for i, cs in enumerate(copy_ss):
-                        with torch.cuda.stream(cs):
-                            if k >= 2:
-                                cs.wait_event(ev_used[b])
-                            for dst, src in zip(sets[b], (Xh, Th, Dh)):
-                                lo, hi = slices(src.shape[0])[i]
-                                dst[lo:hi].copy_(src[lo:hi], non_blocking=True)
-                            ev_copy[b][i].record(cs)
-                    for i in range(n_cs):
-                        stream.wait_event(ev_copy[b][i])
-                    graphs[b].replay()
-                    ev_used[b].record(stream)
-                    d2h()
-                t1.record(stream)
-                torch.cuda.synchronize()
-                return t0.elapsed_time(t1)
-
-            run_e2e(4)
-            E_local = run_e2e(args.steps)
-            e2e_mode = (f"pipelined: H2D of step k+1 ({n_cs} copy streams) overlaps compute of step k "
-                        "(two input buffer sets)")
-        else:
-            Xd, Td, Dd = torch.empty_like(X), torch.empty_like(T), torch.empty_like(D)
-
-            def e2e_step():
-                Xd.copy_(Xh, non_blocking=True)
-                Td.copy_(Th, non_blocking=True)
-                Dd.copy_(Dh, non_blocking=True)
-                step(Xd, Td, Dd)
-                d2h()
-
-            for _ in range(2):
-                e2e_step()
-            torch.cuda.synchronize()
-            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            for k in range(args.steps):
-                flush.zero_()
-                e0[k].record(stream)
-                e2e_step()
-                e1[k].record(stream)
-            torch.cuda.synchronize()
-            E_local = float(sum(a.elapsed_time(b) for a, b in zip(e0, e1)))
-            e2e_mode = "serial: H2D, compute, D2H per step, L2 flushed between steps"
-        E_ms, _ = rank_reduce(dist, dev, E_local, [])
-        h2d = xyz.nbytes + t.nbytes + d.nbytes
-        d2h_bytes = sum(v.numel() * v.element_size() for o in outs for v in o.values())
-        e2e = {"value": tot_q * args.steps / (E_ms * 1e-3), "unit": "ion-queries/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h_bytes, "ms_per_step": E_ms / args.steps, "mode": e2e_mode}
-
-    # ---- roofline of the dominant kernel family ----
-    peak, peak_kind = load_peaks()
-    alg = algorithmic_bytes(dom, st)
-    launches_per_step = max(1, dom_n // max(1, args.steps))
-    per_launch_bytes = alg / launches_per_step
-    avg_ms = dom_ms / max(1, dom_n)
-    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+        XB, TB, DB = torch.empty_like(X), torch.empty_like(T), torch.empty_like(D)
+        graph_b = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph_b):
+            step(XB, TB, DB)
+        graphs = {X.data_ptr(): graph, XB.data_ptr(): graph_b}
+        run = e2e_runner(dev, stream, [(X, T, D), (XB, TB, DB)], (Xh, Th, Dh),
+                         lambda Xs, Ts, Ds: graphs[Xs.data_ptr()].replay(), outs, res_h)
+        run(4)
+        E_ms, _ = rank_reduce(dist, dev, run(steps), [])
+        e2e = {"value": tot_q * steps / (E_ms * 1e-3), "unit": "ion-queries/s",
+               "h2d_bytes_per_step": xyz.nbytes + t.nbytes + d.nbytes,
+               "d2h_bytes_per_step": sum(v.numel() * v.element_size() for o in outs for v in o.values()),
+               "ms_per_step": E_ms / steps,
+               "mode": "pipelined: the H2D of step k+1 overlaps the compute of step k (two input buffer sets)"}
+    hbm_peak, hbm_src = load_hbm_peak()
     kcfg = {name: {"cell_scale": float(tuned[name]["cell_scale"]), "dense_min": int(tuned[name]["dense_min"])}
             for name, _, _ in wl["combos"]}
-    common = {"kernel": dom, "peak_source": peak_kind, "avg_launch_us": avg_ms * 1e3, "launches": dom_n,
-              "timing": "CUDA events around each launch, eager pass of the step with the combinations one after the other",
-              "time_share": shares[dom] / max(1e-12, sum(shares.values())),
-              "shares": {k: round(v / max(1e-12, sum(shares.values())), 4) for k, v in shares.items()}}
-    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-           "algorithmic_bytes_per_launch": per_launch_bytes}
-    if dom == "query":
-        # the pair test is the work: FP32 arithmetic on L2-resident records (DRAM traffic is a few MB)
-        cands = sum(c["candidates"] for c in st["combos"])
-        flops = FLOPS_PER_CANDIDATE * cands / launches_per_step
-        alu_peak, mhz = alu_peak_tflops()
-        alu = flops / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
-        roofline = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu / alu_peak,
-                    "traffic": stored_traffic(wl_name, kcfg), "traffic_unit": "DRAM bytes per launch (ncu)",
-                    "flops_per_launch": flops, "candidate_tests_per_step": cands,
-                    "peak_derivation": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz, 1 op/lane/clock",
-                    "hbm": hbm, **common}
+    roof = rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, stored_traffic(wl_name, kcfg))
+    roof["timing"] = ("CUDA events around every launch on the launching stream, in an eager pass of the step with "
+                      "the combinations one after the other (the timed steps are graph replays)")
+    for g in grids:
+        g.close()
+    return {"value": tot_q * steps / (T_ms * 1e-3), "T_ms": T_ms, "n_queries": n_queries, "n_pairs": n_pairs,
+            "launches": kernels_per_step * steps, "clocks": clocks, "e2e": e2e, "roofline": roof,
+            "kernel_config": kcfg, "autotune": {k: v.get("timings_ms") for k, v in tuned.items()},
+            "workload": wl["desc"], "n_ions": N, "ms_per_step": T_ms / steps, "steps": steps,
+            "neighbour_pairs_per_s": tot_p * steps / (T_ms * 1e-3)}
+
+
+def rank_reduce(dist, device, t_max, sums):
+    """Whole-job numbers across ranks: the slowest rank's time and the summed counts.
+
+    dist is torch.distributed (or None for one process); device is where the reduction
+    tensors live (a CUDA device under NCCL, the CPU under gloo)."""
+    import torch
+
+    if dist is None:
+        return float(t_max), [float(x) for x in sums]
+    tt = torch.tensor([float(t_max)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ss = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
+    dist.all_reduce(ss)
+    return float(tt.item()), [float(x) for x in ss.tolist()]
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def local_rank() -> int:
+    return int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def gpu_index(local: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return int(vis.split(",")[local])
+    return local
+
+
+def run_gpu(args, wl_name, wl):
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = local_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    peaks = ps.measure_peaks()
+
+    if wl.get("sharded"):
+        head = measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks)
+        scaling = "strong"
+        parallelism = (f"z-slabs of equal ion count x{world} (r_cut halo each), one int64 sum all-reduce of the "
+                       f"histograms per combination" if world > 1 else "one GPU, one slab (the whole specimen)")
     else:
-        roofline = {"bound": "hbm", **{k: v for k, v in hbm.items() if k != "algorithmic_bytes_per_launch"},
-                    "traffic": None, **common}
+        head = measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, args.steps, args.warmup,
+                               not args.no_e2e)
+        scaling = "weak"
+        parallelism = f"replicas x{world} (independent specimens, no collective)"
+
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary and wl.get("sharded"):
+        secondary = {}
+        for name in SECONDARY:
+            w2 = resolve(name)
+            r = measure_replica(args, name, w2, dev, None, 1, 0, peaks, 20, 5, False)
+            secondary[name] = {k: r[k] for k in ("workload", "value", "ms_per_step", "steps", "n_queries",
+                                                 "neighbour_pairs_per_s", "kernel_config", "clocks")}
+            secondary[name]["roofline"] = {k: r["roofline"][k] for k in ("achieved", "peak", "unit", "frac", "traffic",
+                                                                         "avg_launch_ms", "time_share")}
+            secondary[name]["smem_atomic_frac"] = r["roofline"]["smem_atomic"]["frac"]
+            secondary[name]["hbm_build_frac"] = r["roofline"]["hbm_build"]["frac"]
 
     forms = None
     if rank == 0 and not args.no_forms:
@@ -918,77 +1095,69 @@ def run_gpu(args, wl_name, wl):
         forms["sdm"] = measure_sdm(args, dev)
         forms["cluster"] = measure_cluster(args, dev)
 
-    # ---- cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import concurrent.futures as cf
-
-        # all host cores: independent oracle runs over consecutive z-slabs of centrals (exact sum)
         cores = host_cores()
-        with cf.ThreadPoolExecutor(max_workers=cores) as pool:
-            orc, parts, frac, nq, _ = oracle_sample_parallel(wl, cloud, pool, cores, target_s=2.0)
-            reps = 0
-            t0 = time.perf_counter()
-            while reps < 3 or time.perf_counter() - t0 < 10.0:
-                oracle_step_parts(orc, parts, wl, pool)
-                reps += 1
-                if time.perf_counter() - t0 > 30.0:
-                    break
-            dt = time.perf_counter() - t0
-        # and one core, for reference
-        orc, samp, frac1, nq1, _ = oracle_sample(wl_name, wl, cloud, target_s=1.0)
-        t1 = time.perf_counter()
-        reps1 = 0
-        while reps1 < 2 or time.perf_counter() - t1 < 3.0:
-            oracle_step(orc, samp, wl)
-            reps1 += 1
-        dt1 = time.perf_counter() - t1
+        cloud = None if wl.get("sharded") else make_cloud(wl_name)
+        orc, parts, pool, nq, desc = oracle_sampled(wl_name, wl, cores, target_s=3.0, cloud=cloud)
+        reps, dt = 0, 0.0
+        while reps < 3 or dt < 10.0:
+            nq, t1 = oracle_steps(orc, parts, pool, wl, 1)
+            reps += 1
+            dt += t1
+            if dt > 30.0:
+                break
+        pool.shutdown()
         cpu = {"value": nq * reps / dt, "unit": "ion-queries/s", "cores": cores, "kind": "oracle",
-               "sample": f"z-slab with {frac:.3f} of the height split in {cores} slabs of centrals (+2 nm halo "
-                         f"each), one host thread each; {nq} centrals, {reps} runs",
-               "value_1core": nq1 * reps1 / dt1}
+               "sample": f"{desc}; {nq} centrals per run, {reps} runs"}
 
     if rank == 0:
         line = {
-            "metric": "ion-queries/s (exact kNN+RDF)", "value": value, "unit": "ion-queries/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n_ions": N, "centrals_per_step": n_queries,
-                       "kernel_config": {k: {"cell_scale": v["cell_scale"], "dense_min": v["dense_min"]}
-                                         for k, v in tuned.items()},
-                       "autotune": {k: v.get("timings_ms") for k, v in tuned.items()},
-                       "neighbour_pairs_per_step": n_pairs, "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x{world} (independent specimens, no collective)",
-                       "combo_streams": len(combo_streams) if combo_streams else 1},
-            "neighbour_pairs_per_s": tot_p * args.steps / (T_ms * 1e-3),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "gpu_launches_per_step": launches / args.steps, "clocks": clocks, "wall_s_timed_loop": wall,
-            "cuda_graph": graph is not None, "forms": forms,
+            "metric": "ion-queries/s (exact kNN+RDF)", "value": head["value"], "unit": "ion-queries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["T_ms"] / args.steps,
+            "higher_is_better": True, "scaling": scaling, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n_ions": int(head.get("n_ions", head.get("n_ions_local", 0))),
+                       "centrals_per_step": head["n_queries"], "neighbour_pairs_per_step": head["n_pairs"],
+                       "kernel_config": head["kernel_config"], "autotune": head["autotune"],
+                       "l2": "flushed between steps (512 MB write); the inputs also exceed L2",
+                       "parallelism": parallelism},
+            "neighbour_pairs_per_s": head["n_pairs"] * args.steps / (head["T_ms"] * 1e-3),
+            "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"], "gpu_launches": head["launches"],
+            "gpu_launches_per_step": head["launches"] / args.steps, "clocks": head["clocks"],
+            "measured_peaks": peaks, "secondary": secondary, "forms": forms,
         }
+        for k in ("slab", "generation_s", "step_ms_min_max"):
+            if k in head:
+                line["config" if k == "slab" else k] = ({**line["config"], "slab_rank0": head[k]} if k == "slab"
+                                                         else head[k])
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
-    for g in grids:
-        g.close()
     return 0
+
+
+def resolve(name):
+    wl = dict(WORKLOADS[name])
+    r0, dr, stop = wl["spec"]
+    wl["bins"] = (r0, dr, int(round((stop - r0) / dr)))
+    return wl
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="needle8m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="needle2g", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clocks-csv", default=None, help="file for the raw nvidia-smi clock samples of the timed region "
                                                          "(default: a temporary file)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--copy-streams", type=int, default=1, help="streams for the e2e input copies (one is fastest)")
-    ap.add_argument("--serial-combos", action="store_true", help="run the type combinations one after the other "
-                    "on one stream (default: one stream each)")
-    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
-    ap.add_argument("--no-forms", action="store_true", help="skip the smoothed-RDF and batched measurements")
+    ap.add_argument("--serial-combos", action="store_true", help="small workloads: run the type combinations one "
+                    "after the other on one stream (default: one stream each)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the smoothed-RDF, batched, SDM and clustering forms")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 8e6-needle and 2e5-cylinder figures")
     ap.add_argument("--batch-rois", type=int, default=256, help="ROIs of the batched measurement (0 skips it)")
     ap.add_argument("--batch-cell-scale", type=float, default=1.0)
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
@@ -998,9 +1167,7 @@ def main():
                     help="measure only this form (no exact step line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    wl = dict(WORKLOADS[args.workload])
-    r0, dr, stop = wl["spec"]
-    wl["bins"] = (r0, dr, int(round((stop - r0) / dr)))
+    wl = resolve(args.workload)
     if args.impl == "reference":
         return run_reference(args, args.workload, wl)
     import __graft_entry__
@@ -1009,7 +1176,7 @@ def main():
     if args.only_form:
         import torch
 
-        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        dev = torch.device("cuda", local_rank())
         torch.cuda.set_device(dev)
         fn = {"soft": measure_soft, "batched": measure_batched, "sdm": measure_sdm,
               "cluster": measure_cluster}[args.only_form]

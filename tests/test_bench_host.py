@@ -33,36 +33,54 @@ def test_candidate_tests_brute_force(stencil, h):
 
 
 def test_stored_traffic_guard():
-    cfg = {"Sc-Sc": {"cell_scale": 1.0, "dense_min": 0}, "Si-Si": {"cell_scale": 1.0, "dense_min": 0}}
-    v = bench.stored_traffic("needle8m", cfg)
+    cfg = {"all-all": {"cell_scale": 0.5, "dense_min": 0}, "Sc-Sc": {"cell_scale": 0.5, "dense_min": 0}}
+    v = bench.stored_traffic("needle2g", cfg)
     # either the stored figure (sources unchanged since the capture) or None; never for another setup
     assert v is None or v > 0
-    assert bench.stored_traffic("needle8m", {**cfg, "Sc-Sc": {"cell_scale": 0.5, "dense_min": 0}}) is None
+    assert bench.stored_traffic("needle2g", {**cfg, "Sc-Sc": {"cell_scale": 1.0, "dense_min": 0}}) is None
     assert bench.stored_traffic("cylinder200k", cfg) is None
 
 
-def test_alu_peak():
-    peak, mhz = bench.alu_peak_tflops()
-    assert peak == pytest.approx(152 * 128 * mhz * 1e6 / 1e12)
-
-
-@pytest.mark.parametrize("parts", [1, 3, 7])
-def test_slab_parts_sum_exactly(orc, parts):
-    """The all-core oracle baseline: independent oracle runs over consecutive z-slabs of centrals
-    (each with an r_cut halo of neighbours) add up to the oracle over the whole slab, histogram for
-    histogram (the halo holds every neighbour within r_cut of a slab's centrals)."""
+@pytest.mark.parametrize("shares", [1, 3, 7])
+def test_small_sample_shares_sum_exactly(orc, shares):
+    """The all-core oracle baseline on a small cloud: the centrals of a z-slab sample split in
+    shares (one host thread each, every share sees all the slab's neighbours) add up to the
+    oracle over the whole sample, histogram for histogram."""
     rng = np.random.default_rng(11)
     n = 6000
     xyz = (rng.random((n, 3)) * np.array([6.0, 6.0, 14.0])).astype(np.float32)
     t = rng.integers(0, 3, n).astype(np.uint8)
     d = (rng.random(n) * 2.0).astype(np.float32)
-    r0, dr, nb = 0.0, 0.05, 20  # stop = 1.0 = the halo
-    ks = [1, 3]
-    whole = bench.slab_parts(xyz, t, d, 0.6, dr * nb, 1)[0]
-    ref = orc.spatstat(*whole, "all", [0, 2], 0.5, r0, dr, nb, ks)
-    got = [orc.spatstat(*p, "all", [0, 2], 0.5, r0, dr, nb, ks) for p in bench.slab_parts(xyz, t, d, 0.6, dr * nb, parts)]
+    wl = dict(bins=(0.0, 0.05, 20), combos=[("x", "all", [0, 2])], ks=[1, 3], dsrf_min=0.5)
+    whole = bench.small_sample(wl, (xyz, t, d), 0.6, 1)[0][0]
+    ref = orc.spatstat(*whole, "all", [0, 2], 0.5, 0.0, 0.05, 20, [1, 3])
+    parts = bench.small_sample(wl, (xyz, t, d), 0.6, shares)[0]
+    got = [orc.spatstat(*p, "all", [0, 2], 0.5, 0.0, 0.05, 20, [1, 3]) for p in parts]
     assert ref["n_central"] > 0
     assert sum(g["n_central"] for g in got) == ref["n_central"]
     np.testing.assert_array_equal(sum(g["rdf"] for g in got), ref["rdf"])
     np.testing.assert_array_equal(sum(g["knn"] for g in got), ref["knn"])
-    np.testing.assert_array_equal(sum(np.asarray(g["not_found"]) for g in got), np.asarray(ref["not_found"]))
+    # and the sample's centrals are exactly those of the whole cloud inside the slab
+    z = xyz[:, 2]
+    z0 = z.min() + 0.5 * (z.max() - z.min()) * 0.4
+    z1 = z0 + 0.6 * (z.max() - z.min())
+    assert ref["n_central"] == int(((z >= z0) & (z < z1) & (d >= 0.5)).sum())
+
+
+def test_needle_sample_is_the_middle_of_the_needle(orc, spec, monkeypatch):
+    """The large-needle sample generates only lattice layers about mid-height; its ions are the
+    full cloud's ions of those layers (same generator), its halo ions are never central."""
+    p = spec.needle_params(5.0, 10.0, 16.0, seed=9)
+    monkeypatch.setattr(bench, "needle_params", lambda name: p)
+    wl = dict(bins=(0.0, 0.01, 100), combos=[("all-all", "all", "all")], ks=[1], dsrf_min=0.5)
+    parts, desc = bench.needle_sample("x", wl, 4, 3)
+    counts = spec.needle_plan(p)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    xyz, t, d = spec.needle(p)
+    mid = len(counts) // 2
+    lo, hi = mid - 2, mid + 2
+    core = set(range(off[lo], off[hi]))
+    n_core = sum(int(np.count_nonzero(~np.isnan(pd))) for _, _, pd in parts)
+    assert n_core == off[hi] - off[lo] == len(core)
+    got = sum(orc.spatstat(*pt, "all", "all", 0.5, 0.0, 0.01, 100, [1])["n_central"] for pt in parts)
+    assert got == int((d[off[lo]:off[hi]] >= 0.5).sum())
