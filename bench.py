@@ -790,17 +790,29 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
     # cell size for the grid shared by the combinations: the autotuner's choice for the dominant
     # combination, timed on a contiguous z-slice of the local cloud (1/32 of it; untimed)
     name0, ctr0, nbr0 = wl["combos"][0]
-    if args.no_autotune:
-        tuned = {"cell_scale": args.cell_scale, "dense_min": args.dense_min, "timings_ms": None}
-    else:
-        from paper_2004_05188_gb300 import autotune
+    from paper_2004_05188_gb300 import autotune
 
-        a = N // 2 - N // 64
-        b = a + N // 32
+    a = N // 2 - N // 64
+    b = a + N // 32
+    if args.no_autotune:
+        tuned = {"cell_scale": args.cell_scale, "dense_min": args.dense_min, "split": int(args.split),
+                 "timings_ms": None}
+    else:
         tuned = autotune.tune(X[a:b], T[a:b], D[a:b], nbr0, ctr0, wl["dsrf_min"], bins, wl["ks"],
-                              candidates=((1.0, 0), (0.5, 0)), reps=2)
-    cs, dm = tuned["cell_scale"], tuned["dense_min"]
-    grid = ps.Grid(N, cs, dm)
+                              candidates=((1.0, 0), (0.5, 0), (0.5, 0, 1)), reps=2)
+    cs, dm, sp = tuned["cell_scale"], tuned["dense_min"], int(tuned.get("split", 0))
+    # the other combinations keep the cell size (one grid) and tune only the query options
+    qopts = {name0: (dm, sp)}
+    tunings = {name0: tuned.get("timings_ms")}
+    for name, ctr, nbr in wl["combos"][1:]:
+        if args.no_autotune or cs >= 1.0:
+            qopts[name] = (dm, sp if cs < 1.0 else 0)
+            continue
+        t2 = autotune.tune(X[a:b], T[a:b], D[a:b], nbr, ctr, wl["dsrf_min"], bins, wl["ks"],
+                           candidates=((cs, 0, 0), (cs, 0, 1)), reps=2)
+        qopts[name] = (int(t2["dense_min"]), int(t2.get("split", 0)))
+        tunings[name] = t2.get("timings_ms")
+    grid = ps.Grid(N, cs, dm, bool(sp))
     nk = len(wl["ks"])
     outs = [dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
                  knn=torch.empty((nk, bins[2]), dtype=torch.int64, device=dev),
@@ -809,6 +821,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
 
     def step(Xs=X, Ts=T, Ds=D):
         for (name, ctr, nbr), o in zip(wl["combos"], outs):
+            grid.set_query_opts(*qopts[name])
             grid.build(Xs, Ts, nbr, r_cut)
             ps.spatstat(grid, Ds, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
         for o in outs:
@@ -818,6 +831,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
     st = {"n_ions": N, "combos": []}
     stencil = 1 if cs >= 1.0 else 2
     for (name, ctr, nbr), o in zip(wl["combos"], outs):
+        grid.set_query_opts(*qopts[name])
         grid.build(X, T, nbr, r_cut)
         ps.spatstat(grid, D, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
         torch.cuda.synchronize()
@@ -874,12 +888,13 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
         del sets, res_h
 
     hbm_peak, hbm_src = load_hbm_peak()
-    kcfg = {name: {"cell_scale": float(cs), "dense_min": int(dm)} for name, _, _ in wl["combos"]}
+    kcfg = {name: {"cell_scale": float(cs), "dense_min": int(qopts[name][0]), "split": int(qopts[name][1])}
+            for name, _, _ in wl["combos"]}
     roof = rooflines(prof, st, args.steps, peaks, hbm_peak, hbm_src, stored_traffic(wl_name, kcfg))
     grid.close()
     res = {"value": value, "T_ms": T_ms, "n_queries": n_queries, "n_pairs": n_pairs, "launches": launches,
            "clocks": clocks, "wall": wall, "e2e": e2e, "roofline": roof, "n_ions_local": N,
-           "kernel_config": kcfg, "autotune": tuned.get("timings_ms"), "generation_s": gen_s,
+           "kernel_config": kcfg, "autotune": tunings, "generation_s": gen_s,
            "slab": {"layers": [int(cuts[rank]), int(cuts[rank + 1])], "halo_layers": halo, "ions_generated": N,
                     "core_ions": int(core[1] - core[0])},
            "step_ms_min_max": [min(step_ms), max(step_ms)]}
@@ -905,12 +920,13 @@ def measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, steps, war
     tuned = {}
     for name, ctr, nbr in wl["combos"]:
         if args.no_autotune:
-            tuned[name] = {"cell_scale": args.cell_scale, "dense_min": args.dense_min}
+            tuned[name] = {"cell_scale": args.cell_scale, "dense_min": args.dense_min, "split": int(args.split)}
         else:
             from paper_2004_05188_gb300 import autotune
 
             tuned[name] = autotune.tune(X, T, D, nbr, ctr, wl["dsrf_min"], bins, wl["ks"])
-    grids = [ps.Grid(N, tuned[name]["cell_scale"], tuned[name]["dense_min"]) for name, _, _ in wl["combos"]]
+    grids = [ps.Grid(N, tuned[name]["cell_scale"], tuned[name]["dense_min"], bool(tuned[name].get("split", 0)))
+             for name, _, _ in wl["combos"]]
     nk = len(wl["ks"])
     outs = [dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
                  knn=torch.empty((nk, bins[2]), dtype=torch.int64, device=dev),
@@ -1000,8 +1016,8 @@ def measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, steps, war
                "ms_per_step": E_ms / steps,
                "mode": "pipelined: the H2D of step k+1 overlaps the compute of step k (two input buffer sets)"}
     hbm_peak, hbm_src = load_hbm_peak()
-    kcfg = {name: {"cell_scale": float(tuned[name]["cell_scale"]), "dense_min": int(tuned[name]["dense_min"])}
-            for name, _, _ in wl["combos"]}
+    kcfg = {name: {"cell_scale": float(tuned[name]["cell_scale"]), "dense_min": int(tuned[name]["dense_min"]),
+                   "split": int(tuned[name].get("split", 0))} for name, _, _ in wl["combos"]}
     roof = rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, stored_traffic(wl_name, kcfg))
     roof["timing"] = ("CUDA events around every launch on the launching stream, in an eager pass of the step with "
                       "the combinations one after the other (the timed steps are graph replays)")
@@ -1162,7 +1178,9 @@ def main():
     ap.add_argument("--batch-cell-scale", type=float, default=1.0)
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
-    ap.add_argument("--no-autotune", action="store_true", help="use --cell-scale/--dense-min instead of the autotuner")
+    ap.add_argument("--split", action="store_true", help="the query in passes (with --no-autotune; ps_grid_opts.split)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --cell-scale/--dense-min/--split instead of the autotuner")
     ap.add_argument("--only-form", choices=["soft", "batched", "sdm", "cluster"],
                     help="measure only this form (no exact step line)")
     args = ap.parse_args()

@@ -100,6 +100,12 @@ typedef struct {
   uint32_t block;     /* reserved (0) */
   uint32_t dense_min; /* cells with at least this many centrals use the CTA kernel that stages the
                          neighbour cells in shared memory with bulk copies; 0 = never */
+  uint32_t split;     /* 1: with cell_scale < 1, an exact query that wants the RDF and no per-central
+                         in-range counts, and central types among the neighbour types, runs in passes:
+                         kNN within the cell edge (27 cells) with a full-radius search only for the
+                         centrals that have fewer than k neighbours there, and the RDF over unordered
+                         pairs (each pair tested once, counted once per central end).  Same results;
+                         0 (default): one combined pass */
 } ps_grid_opts;
 
 typedef struct ps_grid ps_grid; /* opaque; owns its device scratch */
@@ -136,6 +142,9 @@ PS_API int ps_grid_build(ps_grid* g, const float* xyz, const uint8_t* type, int6
 PS_API int ps_build_grid(const float* xyz, const uint8_t* type, int64_t n, const uint64_t nbr_mask[4], float r_cut,
                   const ps_grid_opts* opts, void* stream, ps_grid** out);
 PS_API int ps_grid_destroy(ps_grid* g);
+/* The query options of a grid (ps_grid_opts.dense_min and .split) for its next queries; the cell
+ * size stays.  Host only: takes effect for calls enqueued afterwards. */
+PS_API int ps_grid_set_query_opts(ps_grid* g, uint32_t dense_min, uint32_t split);
 
 /* Grid geometry, read back from the device (synchronises `stream`). */
 typedef struct {
@@ -403,7 +412,7 @@ typedef enum {
   PS_KID_SCAN = 5,       /* exclusive scan of cell counts (3 launches) */
   PS_KID_SCATTER = 6,    /* counting-sort scatter */
   PS_KID_CENTRAL = 7,    /* central reset + selection + cell rank */
-  PS_KID_QUERY = 8,      /* exact kNN + RDF query */
+  PS_KID_QUERY = 8,      /* exact kNN + RDF query (the split query's near-radius kNN pass) */
   PS_KID_EPILOGUE = 9,   /* meta epilogue */
   PS_KID_SOFT_FWD = 10,  /* smoothed RDF forward */
   PS_KID_SOFT_BWD = 11,  /* smoothed RDF adjoint */
@@ -413,7 +422,9 @@ typedef enum {
   PS_KID_CLUSTER = 15,   /* maximum-separation clustering */
   PS_KID_FINALISE = 16,  /* g(r) normalisation */
   PS_KID_PEAKS = 17,     /* throughput microbenchmarks (ps_measure_peaks) */
-  PS_KID_COUNT_ = 18
+  PS_KID_RDF_SYM = 18,   /* RDF over unordered pairs (the split query's third pass) */
+  PS_KID_KNN_FULL = 19,  /* full-radius kNN of the centrals the near pass left (split query) */
+  PS_KID_COUNT_ = 20
 } ps_kernel_id;
 PS_API uint64_t ps_launch_count(void);
 

@@ -68,7 +68,7 @@ class Bins(ctypes.Structure):
 
 class GridOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("cell_scale", ctypes.c_float), ("block", ctypes.c_uint32),
-                ("dense_min", ctypes.c_uint32)]
+                ("dense_min", ctypes.c_uint32), ("split", ctypes.c_uint32)]
 
 
 class GridInfo(ctypes.Structure):
@@ -129,6 +129,7 @@ def lib():
     L.ps_grid_build.argtypes = [P, P, P, i64, P, f32, P]
     L.ps_build_grid.argtypes = [P, P, i64, P, f32, ctypes.POINTER(GridOpts), P, ctypes.POINTER(P)]
     L.ps_grid_destroy.argtypes = [P]
+    L.ps_grid_set_query_opts.argtypes = [P, u32, u32]
     L.ps_grid_get_info.argtypes = [P, ctypes.POINTER(GridInfo), P]
     L.ps_spatstat.argtypes = [P, P, P, f32, Bins, P, u32, P, P, P, P, P, P]
     L.ps_knn_hist.argtypes = [P, P, P, f32, u32, Bins, P, P, P, P]
@@ -162,7 +163,7 @@ def _check(rc: int):
 
 
 KID = dict(reset=1, select=2, geometry=3, count=4, scan=5, scatter=6, central=7, query=8, epilogue=9, soft_fwd=10,
-           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15, finalise=16, peaks=17)
+           soft_bwd=11, batch=12, labels=13, sdm=14, cluster=15, finalise=16, peaks=17, rdf_sym=18, knn_full=19)
 
 
 def measure_peaks(stream=None) -> dict:
@@ -238,10 +239,12 @@ def _check_cloud(xyz, type_, dsrf=None):
 class Grid:
     """A cell grid over the neighbour set of one cloud (ps_grid_create / ps_grid_build)."""
 
-    def __init__(self, n_max: int, cell_scale: float = 1.0, dense_min: int = 0):
+    def __init__(self, n_max: int, cell_scale: float = 1.0, dense_min: int = 0, split: bool = False):
         """cell_scale: cell edge / r_cut (>= 1: 27-cell search; [0.5, 1): 125-cell search).
-        dense_min: cells with at least this many centrals use the shared-memory staged kernel (0: never)."""
-        opts = GridOpts(ctypes.sizeof(GridOpts), float(cell_scale), 0, int(dense_min))
+        dense_min: cells with at least this many centrals use the shared-memory staged kernel (0: never).
+        split: run the exact query in passes where it applies (near-radius kNN with a full-radius
+        fallback, RDF over unordered pairs); same results (see ps_grid_opts.split)."""
+        opts = GridOpts(ctypes.sizeof(GridOpts), float(cell_scale), 0, int(dense_min), int(bool(split)))
         h = ctypes.c_void_p()
         _check(lib().ps_grid_create(int(n_max), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
@@ -259,6 +262,11 @@ class Grid:
         self._refs = (xyz, type_)  # the grid reads these again in every query
         self.n = int(xyz.shape[0])
         self.r_cut = float(r_cut)
+        return self
+
+    def set_query_opts(self, dense_min: int = 0, split: bool = False):
+        """Query options for the next queries on this grid (ps_grid_set_query_opts); the cell size stays."""
+        _check(lib().ps_grid_set_query_opts(self._h, int(dense_min), int(bool(split))))
         return self
 
     def info(self, stream=None) -> dict:
@@ -306,7 +314,8 @@ def spatstat(grid: Grid, dsrf, ctr_types, dsrf_min: float, bins, ks=(), rdf: boo
         out["meta"] = torch.empty(META_HEAD + 2 * nk, dtype=torch.int64, device=dev)
         if per_central:
             out["kth_d2"] = torch.full((nk, grid.n), float("nan"), dtype=torch.float32, device=dev) if nk else None
-            out["n_within"] = torch.full((grid.n,), -1, dtype=torch.int32, device=dev)
+            if per_central != "kth":
+                out["n_within"] = torch.full((grid.n,), -1, dtype=torch.int32, device=dev)
     ks_a = np.ascontiguousarray(ks, np.uint32)
     m, mp = _mask_ptr(ctr_types)
     _check(lib().ps_spatstat(grid.handle, _ptr(dsrf), mp, float(dsrf_min), Bins(r0, dr, nb),

@@ -9,6 +9,10 @@ the cloud (density, type fractions) and on the query (r_max, k):
 * dense_min: cells with at least this many centrals are handled by one CTA
   (8 warps) that stages the neighbour cells in shared memory with bulk copies;
   0 keeps every cell on the warp kernel (one warp per 32 centrals).
+* split: with half-size cells, the query in passes (kNN within the cell edge
+  with a full-radius fallback, the RDF over unordered pairs) instead of one
+  combined pass; it pays where most centrals have k neighbours within the cell
+  edge (dense sets), not for sparse types.
 
 `tune` times every candidate configuration on the caller's data (CUDA events,
 after a warm-up) and returns the fastest.  Results are cached per workload
@@ -20,7 +24,8 @@ import json
 import math
 import os
 
-CANDIDATES = ((1.0, 0), (0.75, 0), (0.5, 0), (1.0, 128))
+# (cell_scale, dense_min[, split])
+CANDIDATES = ((1.0, 0), (0.75, 0), (0.5, 0), (1.0, 128), (0.5, 0, 1))
 
 _cache: dict = {}
 
@@ -69,9 +74,9 @@ def _store(path, data):
 
 def tune(X, T, D, nbr_types, ctr_types, dsrf_min, bins, ks, candidates=CANDIDATES, reps=3, cache_path=None,
          runner=None, key=None):
-    """Return {"cell_scale", "dense_min", "timings_ms", "key", "cached"} for this workload.
+    """Return {"cell_scale", "dense_min", "split", "timings_ms", "key", "cached"} for this workload.
 
-    runner(cell_scale, dense_min) -> milliseconds overrides the GPU timing (tests use it).
+    runner(cell_scale, dense_min, split) -> milliseconds overrides the GPU timing (tests use it).
     """
     if key is None:
         import torch
@@ -93,11 +98,12 @@ def tune(X, T, D, nbr_types, ctr_types, dsrf_min, bins, ks, candidates=CANDIDATE
     if runner is None:
         runner = _gpu_runner(X, T, D, nbr_types, ctr_types, dsrf_min, bins, ks, reps)
     timings = {}
-    for cs, dm in candidates:
-        timings[(cs, dm)] = float(runner(cs, dm))
-    cs, dm = choose(timings)
-    res = {"cell_scale": cs, "dense_min": dm, "key": key,
-           "timings_ms": {f"cell_scale={c},dense_min={d}": round(t, 4) for (c, d), t in timings.items()}}
+    for cand in candidates:
+        cs, dm, sp = (tuple(cand) + (0,))[:3]
+        timings[(cs, dm, sp)] = float(runner(cs, dm, sp))
+    cs, dm, sp = choose(timings)
+    res = {"cell_scale": cs, "dense_min": dm, "split": sp, "key": key,
+           "timings_ms": {f"cell_scale={c},dense_min={d},split={q}": round(t, 4) for (c, d, q), t in timings.items()}}
     _cache[key] = res
     if cache_path:
         disk[key] = res
@@ -115,8 +121,8 @@ def _gpu_runner(X, T, D, nbr_types, ctr_types, dsrf_min, bins, ks, reps):
     r0, dr, nb = bins
     r_cut = (r0 + dr * nb) * (1.0 + 1e-6)
 
-    def run(cs, dm):
-        g = Grid(X.shape[0], cs, dm)
+    def run(cs, dm, sp=0):
+        g = Grid(X.shape[0], cs, dm, bool(sp))
         out = None
         for _ in range(2):
             g.build(X, T, nbr_types, r_cut)

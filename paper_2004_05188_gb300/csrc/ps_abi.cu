@@ -126,7 +126,9 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
   g->cell_scale = cell_scale;
   g->stencil = cell_scale >= 1.0f ? 1 : 2;
   g->block = block;
-  if (opts && opts->struct_size >= sizeof(ps_grid_opts)) g->dense_min = opts->dense_min ? opts->dense_min : 0xFFFFFFFFu;
+  if (opts && opts->struct_size >= offsetof(ps_grid_opts, dense_min) + sizeof(uint32_t))
+    g->dense_min = opts->dense_min ? opts->dense_min : 0xFFFFFFFFu;
+  if (opts && opts->struct_size >= offsetof(ps_grid_opts, split) + sizeof(uint32_t)) g->split = opts->split != 0;
   // cells: a bounding-box grid at the cutoff needs ~n/100 cells for the clouds seen here; the
   // capacity leaves a wide margin (the cell edge grows past it, results do not change)
   const int64_t cap0 = g->stencil == 2 ? g->n_max : g->n_max / 8;
@@ -195,6 +197,13 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
     return cuda_fail(e, "cudaMemset(grid)");
   }
   *out = g;
+  return PS_OK;
+}
+
+int ps_grid_set_query_opts(ps_grid* g, uint32_t dense_min, uint32_t split) {
+  if (!g) return fail(PS_ERR_INVALID_ARG, "ps_grid_set_query_opts: grid is NULL");
+  g->dense_min = dense_min ? dense_min : 0xFFFFFFFFu;
+  g->split = split != 0;
   return PS_OK;
 }
 

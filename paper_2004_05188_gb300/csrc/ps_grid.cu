@@ -111,6 +111,7 @@ __global__ void k_reset(Geo* geo) {
     geo->status = 0;
     geo->work_n = geo->work_n2 = geo->work_n3 = geo->work_n4 = 0;
     geo->work_next = geo->work_next2 = geo->work_next3 = 0;
+    geo->work_next2b = geo->work_next3b = geo->sym_next = 0;
   }
 }
 
@@ -348,6 +349,7 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     cgeo->status = 0;
     cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = cgeo->work_n4 = 0;
     cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
+    cgeo->work_next2b = cgeo->work_next3b = cgeo->sym_next = 0;
   }
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (uint32_t c = tid; c < nc; c += stride) count[c] = 0;
@@ -629,6 +631,7 @@ __global__ void __launch_bounds__(kScanThreads) k_central_subset(const float4* _
     cgeo->status = 0;
     cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = cgeo->work_n4 = 0;
     cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
+    cgeo->work_next2b = cgeo->work_next3b = cgeo->sym_next = 0;
     if (nr == 0) pfx[0] = 0, cgeo->n_sel = 0;
   }
   {

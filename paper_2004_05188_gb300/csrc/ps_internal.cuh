@@ -80,6 +80,9 @@ struct Geo {
   uint32_t work_n3;    // items from the back of witem[] (sparse cells of central lists), witem[cap-1] downwards
   uint32_t work_next3; // light items taken so far (query kernel: 32 at a time)
   uint32_t work_n4;    // very heavy warp items (exact query), listed apart and taken before the others
+  uint32_t work_next2b;  // second pass over the same items (the exact query's full-radius kNN fallback)
+  uint32_t work_next3b;
+  uint32_t sym_next;     // cells taken by the symmetric RDF pass (32 at a time)
 };
 
 // Warp items with at least this many centrals per cell are listed first (largest work first).
@@ -153,6 +156,7 @@ struct ps_grid {
   uint32_t item_cap = 0;       // capacity of the warp item list
   int stencil = 1;             // neighbour cells searched on each side (1: cell >= r_cut, 2: cell >= r_cut/2)
   bool pack_type = false;      // records carry (index << 8 | type) instead of the index (batched sweeps)
+  bool split = false;          // exact query in passes: near-radius kNN + fallback, symmetric RDF (ps_grid_opts.split)
   uint64_t nbr_mask[4] = {0, 0, 0, 0};  // type set of the last build's neighbour records
   uint32_t* sel = nullptr;     // [n_max] selected ion indices
   uint2* cr = nullptr;         // [n_max] (cell, rank) of selected ions

@@ -56,6 +56,14 @@ struct QueryArgs {
   float* kth;
   uint32_t* nwithin;
   int64_t n;  // ions in the cloud (stride of kth)
+  // passes of the split query (zero / null for the combined one)
+  float emax_near;        // > 0: kNN within this squared range only; a central with fewer than k_need
+                          // neighbours there is marked in need[] instead of being counted
+  uint32_t* need;         // per central record: 1 = needs the full-radius search (near pass writes it)
+  int fallback;           // 1: only the centrals marked in need[] (the full-radius kNN pass)
+  uint32_t* next_front;   // work counters of the front (heavy) and back (light) items
+  uint32_t* next_light;
+  const uint32_t* pfx;    // symmetric RDF pass: central prefix over the neighbour records
 };
 
 template <int K>
@@ -171,6 +179,20 @@ struct Hist {
       ++binned;
     } else {
       ++below;
+    }
+  }
+
+  // one in-range unordered pair of weight w (the number of its central ends)
+  __device__ __forceinline__ void pair_w(const QueryArgs& a, float d2, uint32_t w, uint64_t& binned, uint64_t& below) {
+    if (d2 >= E0) {
+      const uint32_t b = bin_index(d2, sE, nb, r0f, inv_dr);
+      if (priv)
+        atomicAdd(&s_rdfw[b], w);
+      else
+        atomicAdd(&s_rdf[b], (unsigned long long)w);
+      binned += w;
+    } else {
+      below += w;
     }
   }
 
@@ -312,6 +334,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   const Geo ng = *a.ngeo;
   const uint32_t n_hi = a.cgeo->work_n4, n_front = n_hi + a.cgeo->work_n2, n_light = a.cgeo->work_n3;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
+  const float erange = a.emax_near > 0.f ? a.emax_near : H.Emax;  // squared search range of this pass
   uint64_t my_binned = 0, my_below = 0;
   float4* buf = s_buf[w];
   float* wlist = s_hits[w];
@@ -322,7 +345,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   // ---- items from the front: dense cells, the very heavy ones first ----
   for (;;) {
     uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(&a.cgeo->work_next2, 1u);
+    if (lane == 0) item = atomicAdd(a.next_front, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n_front) break;
     const uint2 it = item < n_hi ? a.whi[item] : a.witem[item - n_hi];
@@ -366,11 +389,13 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
       const uint32_t lg = L == 8u ? 3u : (L == 4u ? 2u : (L == 2u ? 1u : 0u));
       const uint32_t sub = lane & (L - 1u), ci = lane >> lg;
       const uint32_t n_it = 8u >> lg;  // pair tests per lane per half-batch
-      const bool valid = ci < cnt;
+      bool valid = ci < cnt;
+      if (a.fallback && valid) valid = a.need[c0 + ci] != 0u;
+      if (a.fallback && __ballot_sync(0xffffffffu, valid) == 0u) continue;  // no central of this item to redo
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) p = a.crec[c0 + ci];
       const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
-      const float emax = valid ? H.Emax : -INFINITY;  // lanes without a central never hit
+      const float emax = valid ? erange : -INFINITY;  // lanes without a central never hit
       const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
       const uint32_t lt = (1u << lane) - 1u;
       float top[KK];
@@ -468,13 +493,18 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
       }
       if (valid && sub == 0) {
         if (a.nwithin) a.nwithin[pidx] = within;
-        if (KMAX > 0)
-          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
+        if (KMAX > 0) {
+          const bool found = !(a.emax_near > 0.f) || topk_get(top, a.k_need - 1) < a.emax_near;
+          if (a.emax_near > 0.f) a.need[c0 + ci] = found ? 0u : 1u;
+          if (found)
+            for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
+        }
       }
     } else {
       // few centrals, many candidates: the lanes split the candidates of each central and
       // merge their sorted lists by shuffles
       for (uint32_t ci = 0; ci < cnt; ++ci) {
+        if (a.fallback && a.need[c0 + ci] == 0u) continue;  // warp-uniform
         const float4 p = a.crec[c0 + ci];
         const uint32_t pidx = __float_as_uint(p.w);
         float top[KK];
@@ -485,7 +515,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         for (uint32_t b = 0; b < n_cand; b += 32) {
           const float4 q = fetch(b + lane, rr);
           const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-          if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
+          if (d2 < erange && __float_as_uint(q.w) != pidx) {
             ++within;
             H.pair(a, d2, my_binned, my_below);
             if (KMAX > 0) topk_insert(top, d2);
@@ -500,9 +530,10 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           wcount = 0;
         }
         if (KMAX > 0) {
-          // merge the 32 sorted lane lists: pop the warp minimum k_need times
+          // merge the 32 sorted lane lists: pop the warp minimum k_need times (ranks kept in kq)
+          float m = INFINITY;
           for (uint32_t rank = 0; rank < a.k_need; ++rank) {
-            float m = top[0];
+            m = top[0];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
             const uint32_t bal = __ballot_sync(0xffffffffu, top[0] == m);
@@ -511,10 +542,16 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
               for (int t = 0; t < KK - 1; ++t) top[t] = top[t + 1];
               top[KK - 1] = INFINITY;
             }
-            if (lane == 0)
-              for (uint32_t q = 0; q < a.n_k; ++q)
-                if (a.ks[q] == rank + 1) H.kth(a, q, m, pidx);
+            if (lane == 0) kq[rank] = m;
           }
+          __syncwarp();
+          if (lane == 0) {
+            const bool found = !(a.emax_near > 0.f) || m < a.emax_near;
+            if (a.emax_near > 0.f) a.need[c0 + ci] = found ? 0u : 1u;
+            if (found)
+              for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, kq[a.ks[q] - 1], pidx);
+          }
+          __syncwarp();
         }
       }
     }
@@ -530,7 +567,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   const uint32_t take = min(32u, max(1u, (n_light + n_warps - 1) / n_warps));
   for (;;) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.cgeo->work_next3, take);
+    if (lane == 0) base = atomicAdd(a.next_light, take);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_light) break;
     uint32_t c = 0, f = 0, cnt = 0;
@@ -551,7 +588,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     for (uint32_t q = 0; q < cnt; ++q) cl_rec[inc - cnt + q] = f + q, cl_cell[inc - cnt + q] = c;
     __syncwarp();
     for (uint32_t r0 = 0; r0 < total; r0 += 32) {
-      const bool valid = r0 + lane < total;
+      bool valid = r0 + lane < total;
+      if (a.fallback && valid) valid = a.need[cl_rec[r0 + lane]] != 0u;
       uint32_t rowc = 0;  // increments of the warp row by this lane
       if (valid) {
         const uint32_t ce = cl_cell[r0 + lane];
@@ -573,7 +611,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
             for (uint32_t j = a.nstart[row + xlo]; j < j1; ++j) {
               const float4 q = __ldg(a.nrec + j);
               const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-              if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
+              if (d2 < erange && __float_as_uint(q.w) != pidx) {
                 ++within;
                 if (RDF) {
                   if (within <= kRowLaneCap)
@@ -587,8 +625,12 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
         rowc = within < kRowLaneCap ? within : kRowLaneCap;
         if (a.nwithin) a.nwithin[pidx] = within;
-        if (KMAX > 0)
-          for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
+        if (KMAX > 0) {
+          const bool found = !(a.emax_near > 0.f) || topk_get(top, a.k_need - 1) < a.emax_near;
+          if (a.emax_near > 0.f) a.need[cl_rec[r0 + lane]] = found ? 0u : 1u;
+          if (found)
+            for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
+        }
       }
       if (RDF) {
         // a round adds at most 32 * 2^25 = 2^30 to the row: flushed at 2^31, it never wraps
@@ -728,6 +770,214 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
   if (tid == 0 && s_timeout) atomicCAS((int*)&a.cgeo->status, 0, (int)PS_ERR_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// symmetric RDF pass: every unordered pair of neighbour records once
+//
+// The RDF counts ordered pairs (i central, j neighbour, j != i).  When the centrals are
+// neighbour records, an unordered pair {i, j} contributes c_i + c_j (c = 1 for a central
+// record), and d2_ij == d2_ji bit for bit (x_j - x_i == -(x_i - x_j) in IEEE arithmetic), so
+// each pair is tested once, from the lower of its two cells: the half of the stencil with
+// (dz > 0) or (dz == 0 and dy > 0) or (dz == dy == 0 and dx > 0), plus the pairs i < j inside
+// the cell.  A warp takes 32 cells at a time, and for each non-empty cell runs its records (32
+// at a time) as lanes against the half stencil's records, staged 32 at a time and tested two
+// at a time with packed float32 math; the hits (d2, weight) are compacted into a warp list and
+// binned into the warp's 32-bit shared row by all lanes.  The flags come from the central
+// prefix pfx over the records (c_j = pfx[j+1] - pfx[j]).
+// ---------------------------------------------------------------------------
+
+// half-stencil run r of cell c: full x-runs of the rows with dz > 0 (all dy) and of the rows
+// dz == 0, dy > 0; the row dz == dy == 0 from cx + 1 on.  (2s+1)s + s + 1 runs.
+__device__ __forceinline__ void sym_run(const QueryArgs& a, const Geo& ng, uint32_t c, uint32_t r, uint32_t& src,
+                                        uint32_t& len) {
+  const int s = a.stencil, W = 2 * s + 1;
+  const uint32_t cx = c % ng.dims[0], cy = (c / ng.dims[0]) % ng.dims[1], cz = c / (ng.dims[0] * ng.dims[1]);
+  src = 0;
+  len = 0;
+  int dy, dz;
+  uint32_t xlo = cx >= (uint32_t)s ? cx - s : 0;
+  if ((int)r < W * s) {
+    dz = 1 + (int)r / W;
+    dy = (int)r % W - s;
+  } else if ((int)r < W * s + s) {
+    dz = 0;
+    dy = 1 + ((int)r - W * s);
+  } else if ((int)r == W * s + s) {
+    dz = 0;
+    dy = 0;
+    xlo = cx + 1;
+  } else {
+    return;
+  }
+  const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
+  const int y = (int)cy + dy, z = (int)cz + dz;
+  if (y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2] && xlo <= xhi) {
+    const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+    src = a.nstart[row + xlo];
+    len = a.nstart[row + xhi + 1] - src;
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
+  griddep_wait();
+  griddep_launch();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float4 s_buf[8][32];
+  __shared__ float2 s_hits[8][32 * kHalf];  // per warp: (d2, weight) of one half-batch's hits
+  __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
+  Hist<true> H;
+  H.init(a, smem, 0, true);
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
+  const Geo ng = *a.ngeo;
+  const uint32_t n_cells = ng.n_cells;
+  const int s = a.stencil, n_runs = (2 * s + 1) * s + s + 1;
+  uint64_t my_binned = 0, my_below = 0;
+  float* bf = reinterpret_cast<float*>(s_buf[w]);
+  float2* wlist = s_hits[w];
+  uint32_t* rsrc = s_rsrc[w];
+  uint32_t* rpre = s_rpre[w];
+  const float E_max = H.Emax;
+
+  // cells per take: 32, or fewer when the grid is small, so that every warp gets work (about four
+  // takes per warp)
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t take = min(32u, max(1u, (n_cells + 4 * n_warps - 1) / (4 * n_warps)));
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.cgeo->sym_next, take);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_cells) break;
+    uint32_t s0 = 0, s1 = 0;
+    if (lane < take && base + lane < n_cells) s0 = a.nstart[base + lane], s1 = a.nstart[base + lane + 1];
+    uint32_t todo = __ballot_sync(0xffffffffu, s1 > s0);
+    while (todo) {
+      const int src_lane = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const uint32_t c = base + (uint32_t)src_lane;
+      const uint32_t a0 = __shfl_sync(0xffffffffu, s0, src_lane), a1 = __shfl_sync(0xffffffffu, s1, src_lane);
+      // run table of the half stencil
+      uint32_t src = 0, len = 0;
+      sym_run(a, ng, c, lane, src, len);
+      uint32_t pre = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= (uint32_t)o) pre += y;
+      }
+      const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
+      __syncwarp();
+      if (lane < (uint32_t)n_runs) {
+        rsrc[lane] = src;
+        rpre[lane + 1] = pre;
+      }
+      if (lane == 0) rpre[0] = 0;
+      __syncwarp();
+
+      // candidate at virtual position pos (runs concatenated), its central flag in .w
+      auto fetch = [&](uint32_t pos, int& rr) -> float4 {
+        if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        while (pos >= rpre[rr + 1]) ++rr;
+        const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
+        float4 q = __ldg(a.nrec + j);
+        q.w = (float)(__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+        return q;
+      };
+
+      for (uint32_t i0 = a0; i0 < a1; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const bool valid = i < a1;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        float ci = 0.f;
+        if (valid) {
+          p = __ldg(a.nrec + i);
+          ci = (float)(__ldg(a.pfx + i + 1) - __ldg(a.pfx + i));
+        }
+        const float emax = valid ? E_max : -INFINITY;
+        // pairs inside the cell: j in (i, a1), each lane on its own (a small share of the pairs)
+        {
+          uint32_t inc = 0;
+          if (valid) {
+            const bool big = a1 - a0 > (1u << 20);  // per-lane increments stay far below the row's 2^32
+            for (uint32_t j = i + 1; j < a1; ++j) {
+              const float4 q = __ldg(a.nrec + j);
+              const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+              const uint32_t wt = (uint32_t)ci + (__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+              if (d2 < E_max && wt) {
+                if (big) {
+                  if (d2 >= H.E0)
+                    atomicAdd((unsigned long long*)&a.rdf[bin_index(d2, H.sE, H.nb, H.r0f, H.inv_dr)],
+                              (unsigned long long)wt), my_binned += wt;
+                  else
+                    my_below += wt;
+                } else {
+                  H.pair_w(a, d2, wt, my_binned, my_below);
+                  inc += wt;
+                }
+              }
+            }
+          }
+          wcount += __reduce_add_sync(0xffffffffu, inc);
+          if (wcount >= (1ull << 31)) {
+            H.flush_warp(a);
+            wcount = 0;
+          }
+        }
+        // the half stencil: 32 candidates per coalesced load, staged as 16 interleaved pairs
+        // (xa xb ya yb za zb ca cb), tested two at a time
+        const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
+        const unsigned long long pc = f2_pack(ci, ci);
+        int rr = 0;
+        float4 nxt = fetch(lane, rr);
+        for (uint32_t b = 0; b < n_cand; b += 32) {
+          __syncwarp();
+          {
+            float* d = bf + (lane >> 1) * 8 + (lane & 1);
+            d[0] = nxt.x, d[2] = nxt.y, d[4] = nxt.z, d[6] = nxt.w;
+          }
+          __syncwarp();
+          nxt = fetch(b + 32 + lane, rr);
+#pragma unroll 1
+          for (int half = 0; half < 2; ++half) {
+            uint32_t nh = 0;  // hits in the warp list (uniform)
+#pragma unroll 2
+            for (uint32_t u = 0; u < 8; ++u) {
+              const uint32_t t = 8 * half + u;
+              const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
+              const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
+              float d2a, d2b;
+              dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
+              float wa, wb;
+              f2_unpack(f2_add(zw.y, pc), wa, wb);
+              const bool ha = d2a < emax && wa > 0.f;
+              const bool hb = d2b < emax && wb > 0.f;
+              const uint32_t ba = __ballot_sync(0xffffffffu, ha);
+              if (ha) wlist[nh + __popc(ba & lt)] = make_float2(d2a, wa);
+              nh += __popc(ba);
+              const uint32_t bb = __ballot_sync(0xffffffffu, hb);
+              if (hb) wlist[nh + __popc(bb & lt)] = make_float2(d2b, wb);
+              nh += __popc(bb);
+            }
+            __syncwarp();
+            for (uint32_t h = lane; h < nh; h += 32) {
+              const float2 e = wlist[h];
+              H.pair_w(a, e.x, (uint32_t)e.y, my_binned, my_below);
+            }
+            __syncwarp();
+            wcount += 2ull * nh;
+            if (wcount >= (1ull << 31)) {
+              H.flush_warp(a);
+              wcount = 0;
+            }
+          }
+        }
+      }
+    }
+  }
+  H.flush(a);
+  add_pair_counters(a, my_binned, my_below);
+}
+
 // Writes n_central and the device status into the meta array.
 __global__ void k_query_epilogue(const Geo* __restrict__ ngeo, const Geo* __restrict__ cgeo, uint64_t* meta) {
   griddep_wait();
@@ -742,6 +992,7 @@ __global__ void k_query_epilogue(const Geo* __restrict__ ngeo, const Geo* __rest
 
 template <int KMAX, bool RDF>
 static int launch_query(const ps_grid* g, const QueryArgs& qa, uint32_t smem_cta, uint32_t smem_warp, cudaStream_t s) {
+  const uint32_t kid = qa.fallback ? PS_KID_KNN_FULL : PS_KID_QUERY;
   auto kw = k_query_warp<KMAX, RDF>;
   PS_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp));
   int per_sm_w = 0;
@@ -753,9 +1004,9 @@ static int launch_query(const ps_grid* g, const QueryArgs& qa, uint32_t smem_cta
     int per_sm_c = 0;
     PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kc, 256, smem_cta));
     if (per_sm_c < 1) return fail(PS_ERR_UNSUPPORTED, "query kernel does not fit on an SM");
-    PS_LAUNCH(PS_KID_QUERY, s, PS_CUDA(launch_pdl(kc, g->num_sms * per_sm_c, 256, smem_cta, s, qa)));
+    PS_LAUNCH(kid, s, PS_CUDA(launch_pdl(kc, g->num_sms * per_sm_c, 256, smem_cta, s, qa)));
   }
-  PS_LAUNCH(PS_KID_QUERY, s, PS_CUDA(launch_pdl(kw, g->num_sms * per_sm_w, 256, smem_warp, s, qa)));
+  PS_LAUNCH(kid, s, PS_CUDA(launch_pdl(kw, g->num_sms * per_sm_w, 256, smem_warp, s, qa)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -805,6 +1056,8 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.kth = d_kth;
   qa.nwithin = d_nwithin;
   qa.n = g->n;
+  qa.next_front = &g->ctr.geo->work_next2;
+  qa.next_light = &g->ctr.geo->work_next3;
 
   const bool rdf = d_rdf != nullptr;
   ZeroOut z;  // the outputs are zeroed by the central-list reset kernel
@@ -827,7 +1080,40 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.stage_cap = (stage_bytes / 16) & ~7u;
   const uint32_t smem_cta = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap).total;
   const uint32_t smem_warp = smem_layout(bins.n_bins, n_k, rdf, 0, true).total;
-  if (n_k > 0 || rdf) {
+  bool subset = !g->pack_type;
+  for (int w = 0; w < 4; ++w) subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
+  if (g->split && subset && rdf && d_nwithin == nullptr && g->stencil == 2 && g->dense_min == 0xFFFFFFFFu) {
+    // the query in passes: (1) kNN within the cell edge r_cut * cell_scale (27 cells of the
+    // grid), centrals with fewer than k_need neighbours there marked; (2) the full-radius kNN
+    // of the marked centrals; (3) the RDF over unordered pairs
+    if (n_k > 0) {
+      QueryArgs qn = qa;
+      const double rk = (double)g->r_cut * (double)g->cell_scale;
+      double e = bins.r0 + (double)bins.n_bins * bins.dr;
+      const float Emax = (float)(e * e), Ek = (float)(rk * rk);
+      qn.emax_near = Ek < Emax ? Ek : Emax;
+      qn.stencil = 1;
+      qn.need = g->sel;  // free between a build and the next one (the counting sort's index list)
+      rc = dispatch_k<false>(g, qn, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
+      if (rc) return rc;
+      QueryArgs qf = qa;
+      qf.fallback = 1;
+      qf.need = g->sel;
+      qf.next_front = &g->ctr.geo->work_next2b;
+      qf.next_light = &g->ctr.geo->work_next3b;
+      rc = dispatch_k<false>(g, qf, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
+      if (rc) return rc;
+    }
+    QueryArgs qs = qa;
+    qs.n_k = 0;
+    qs.pfx = reinterpret_cast<const uint32_t*>(g->cr);  // written by the central-list compaction
+    const uint32_t smem_sym = smem_layout(bins.n_bins, 0, true, 0, true).total;
+    PS_CUDA(cudaFuncSetAttribute(k_rdf_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sym));
+    int per_sm = 0;
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rdf_sym, 256, smem_sym));
+    if (per_sm < 1) return fail(PS_ERR_UNSUPPORTED, "symmetric RDF kernel does not fit on an SM");
+    PS_LAUNCH(PS_KID_RDF_SYM, s, PS_CUDA(launch_pdl(k_rdf_sym, g->num_sms * per_sm, 256, smem_sym, s, qs)));
+  } else if (n_k > 0 || rdf) {
     rc = rdf ? dispatch_k<true>(g, qa, smem_cta, smem_warp, s) : dispatch_k<false>(g, qa, smem_cta, smem_warp, s);
     if (rc) return rc;
   }

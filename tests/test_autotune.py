@@ -25,21 +25,27 @@ def test_choose_keeps_default_within_margin():
 
 def test_tune_uses_runner_and_caches(tmp_path):
     calls = []
+    t = {(1.0, 0, 0): 3.0, (0.75, 0, 0): 2.5, (0.5, 0, 0): 1.0, (1.0, 128, 0): 4.0, (0.5, 0, 1): 0.6}
 
-    def runner(cs, dm):
-        calls.append((cs, dm))
-        return {(1.0, 0): 3.0, (0.75, 0): 2.5, (0.5, 0): 1.0, (1.0, 128): 4.0}[(cs, dm)]
+    def runner(cs, dm, sp):
+        calls.append((cs, dm, sp))
+        return t[(cs, dm, sp)]
 
     path = str(tmp_path / "tune.json")
     r = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1",
                       cache_path=path)
-    assert (r["cell_scale"], r["dense_min"], r["cached"]) == (0.5, 0, False)
-    assert len(calls) == 4
+    assert (r["cell_scale"], r["dense_min"], r["split"], r["cached"]) == (0.5, 0, 1, False)
+    assert len(calls) == 5
     r2 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1")
-    assert r2["cached"] and len(calls) == 4
+    assert r2["cached"] and len(calls) == 5
     with open(path) as f:
         assert json.load(f)["k1"]["cell_scale"] == 0.5
     autotune._cache.clear()
     r3 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1",
                        cache_path=path)
-    assert r3["cached"] and len(calls) == 4
+    assert r3["cached"] and len(calls) == 5
+    # two-element candidates are (cell_scale, dense_min) with split off
+    autotune._cache.clear()
+    r4 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k2",
+                       candidates=((1.0, 0), (0.5, 0)))
+    assert (r4["cell_scale"], r4["split"]) == (0.5, 0)

@@ -33,11 +33,11 @@ def test_candidate_tests_brute_force(stencil, h):
 
 
 def test_stored_traffic_guard():
-    cfg = {"all-all": {"cell_scale": 0.5, "dense_min": 0}, "Sc-Sc": {"cell_scale": 0.5, "dense_min": 0}}
+    cfg = {"all-all": {"cell_scale": 0.5, "dense_min": 0, "split": 1}, "Sc-Sc": {"cell_scale": 0.5, "dense_min": 0, "split": 1}}
     v = bench.stored_traffic("needle2g", cfg)
     # either the stored figure (sources unchanged since the capture) or None; never for another setup
     assert v is None or v > 0
-    assert bench.stored_traffic("needle2g", {**cfg, "Sc-Sc": {"cell_scale": 1.0, "dense_min": 0}}) is None
+    assert bench.stored_traffic("needle2g", {**cfg, "Sc-Sc": {"cell_scale": 1.0, "dense_min": 0, "split": 0}}) is None
     assert bench.stored_traffic("cylinder200k", cfg) is None
 
 
