@@ -126,11 +126,12 @@ def stored_traffic(workload: str, kernel_config: dict):
     return None
 
 
-def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26):
+def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26, all_records=False):
     """Central x candidate tests one query makes on this grid: for every central, the neighbour
     records in the (2*stencil+1)^3 cells around its cell (clipped at the grid's faces).
     Counted with plain torch ops from the grid geometry (reporting only, untimed), in chunks of
-    ions so that the temporaries stay small beside a 2e9-ion cloud."""
+    ions so that the temporaries stay small beside a 2e9-ion cloud.  all_records: every neighbour
+    record counts as a central (no type or d_srf filter)."""
     import torch
 
     import paper_2004_05188_gb300 as ps
@@ -164,7 +165,10 @@ def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26):
     cnt = cnt.reshape(-1)
     tot = 0
     for a in range(0, n, chunk):
-        cm = lc[T[a:a + chunk].long()] & (D[a:a + chunk] >= dsrf_min)
+        if all_records:  # every neighbour record as a central (the symmetric RDF pass)
+            cm = ln[T[a:a + chunk].long()]
+        else:
+            cm = lc[T[a:a + chunk].long()] & (D[a:a + chunk] >= dsrf_min)
         tot += int(cnt[cells(X[a:a + chunk][cm])].sum().item())
     return tot
 
@@ -653,7 +657,9 @@ def measure_batched(args, dev):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-FAMS = ["reset", "select", "geometry", "count", "scan", "scatter", "central", "query", "epilogue"]
+FAMS = ["reset", "select", "geometry", "count", "scan", "scatter", "central", "query", "knn_full", "rdf_sym",
+        "epilogue"]
+QUERY_FAMS = ("query", "knn_full", "rdf_sym")  # the pair tests: one pass, or the near kNN, fallback and RDF passes
 BUILD_FAMS = ("select", "geometry", "count", "scan", "scatter", "central")
 
 
@@ -662,7 +668,8 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
     throughput (its bound) and against the measured shared-atomic rate (its RDF increments), and
     the build kernels against the measured HBM copy bandwidth.  prof: {family: (launches, ms)}
     summed over `steps` steps; st: per-step counts of every combination."""
-    q_n, q_ms = prof["query"]
+    q_n = sum(prof[f][0] for f in QUERY_FAMS)
+    q_ms = sum(prof[f][1] for f in QUERY_FAMS)
     cands = sum(c["candidates"] for c in st["combos"]) * steps
     pairs = sum(c["n_pairs_local"] for c in st["combos"]) * steps
     alu_peak = max(peaks["fp32_scalar_gops"], peaks["fp32_packed_gops"]) * 1e-3  # TFLOP/s
@@ -673,7 +680,8 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
     b_ms = sum(prof[f][1] for f in BUILD_FAMS)
     tot_ms = sum(v[1] for v in prof.values())
     return {
-        "bound": "alu", "kernel": "query (k_query_warp)", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+        "bound": "alu", "kernel": "query: k_query_warp (one pass, or near kNN + full-radius fallback) and k_rdf_sym",
+        "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
         "frac": alu / alu_peak if alu_peak > 0 else None,
         "peak_source": f"measured: ps_measure_peaks FP32 add/multiply, {peaks['num_sms']} SMs at "
                        f"{peaks['sm_mhz']:.0f} MHz (scalar {peaks['fp32_scalar_gops']:.0f}, packed f32x2 "
@@ -683,6 +691,7 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
         "per_unit": f"{FLOPS_PER_CANDIDATE} FP32 operations per candidate test (3 sub, 3 mul, 2 add, 1 compare)",
         "candidate_tests_per_step": cands // max(1, steps), "flops_per_launch": FLOPS_PER_CANDIDATE * cands / max(1, q_n),
         "launches": q_n, "avg_launch_ms": q_ms / max(1, q_n),
+        "pass_ms_per_step": {f: prof[f][1] / max(1, steps) for f in QUERY_FAMS},
         "timing": "CUDA events around every launch on the launching stream, inside the timed region",
         "time_share": q_ms / tot_ms if tot_ms > 0 else None,
         "shares": {k: round(v[1] / tot_ms, 5) for k, v in prof.items()} if tot_ms > 0 else None,
@@ -699,8 +708,12 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
     }
 
 
-def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil):
-    """Counts of one combination after its build + query (reporting only, untimed)."""
+def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil, split=False):
+    """Counts of one combination after its build + query (reporting only, untimed).  candidates:
+    the distance tests of the query -- one pass: every central against its stencil; in passes
+    (split): every central against its 27-cell stencil (near kNN) plus every unordered pair of
+    records in each other's stencil once (symmetric RDF), the few full-radius fallback searches
+    not counted."""
     meta = o["meta"].cpu().numpy()
     if meta[3] != 0:
         raise RuntimeError(f"device status {meta[3]} for {name}")
@@ -708,9 +721,16 @@ def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil):
     mc, mn = ps.type_mask(ctr), ps.type_mask(nbr)
     lut = np.array([bool((int(mc[v >> 6]) >> (v & 63)) & 1) for v in range(256)])
     n_typed = sum(int(np.count_nonzero(lut[t_host[a:a + (1 << 26)]])) for a in range(0, t_host.shape[0], 1 << 26))
+    subset = bool(np.all((mc & ~mn) == 0))
+    if split and subset and stencil == 2:
+        near = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, 1) if wl["ks"] else 0
+        full = candidate_tests(X, T, D, nbr, nbr, wl["dsrf_min"], info, 2, all_records=True)
+        cands = near + (full - info["n_nbr"]) // 2
+    else:
+        cands = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil)
     return dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
-                n_ctr_typed=n_typed, n_pairs_local=int(meta[1]), subset=bool(np.all((mc & ~mn) == 0)),
-                candidates=candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil))
+                n_ctr_typed=n_typed, n_pairs_local=int(meta[1]), subset=subset, candidates=cands,
+                split=bool(split and subset and stencil == 2))
 
 
 def e2e_runner(dev, stream, sets, hosts, step, outs, res_h):
@@ -835,7 +855,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
         grid.build(X, T, nbr, r_cut)
         ps.spatstat(grid, D, ctr, wl["dsrf_min"], bins, wl["ks"], out=o, check=False)
         torch.cuda.synchronize()
-        st["combos"].append(combo_stats(ps, grid, o, name, ctr, nbr, X, T, D, t, wl, stencil))
+        st["combos"].append(combo_stats(ps, grid, o, name, ctr, nbr, X, T, D, t, wl, stencil, bool(qopts[name][1])))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -960,7 +980,8 @@ def measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, steps, war
     st = {"n_ions": N, "combos": []}
     for (name, ctr, nbr), g, o in zip(wl["combos"], grids, outs):
         stencil = 1 if tuned[name]["cell_scale"] >= 1.0 else 2
-        st["combos"].append(combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t, wl, stencil))
+        st["combos"].append(combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t, wl, stencil,
+                                        bool(tuned[name].get("split", 0))))
     n_queries = sum(c["n_central"] for c in st["combos"])
     n_pairs = sum(c["n_pairs_local"] for c in st["combos"])
     for _ in range(warmup):

@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
-  __shared__ float s_hits[8][32 * kHalf];  // per warp: the in-range hits of one half-batch
-  __shared__ float s_kq[8][32 * kHalf];    // per warp: kNN insertion queue, [slot][lane]
+  __shared__ float s_hits[8][32 * kHalf + 32];  // per warp: the in-range hits of one half-batch + a trash row
+  __shared__ float s_kq[8][32 * kHalf + 32];    // per warp: kNN insertion queue, [slot][lane] + a spare row
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   constexpr int KK = KMAX > 0 ? KMAX : 1;
   Hist<RDF> H;
@@ -431,18 +431,20 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
             const bool hb = d2b < emax && __float_as_uint(wb) != pidx;
             within += (uint32_t)ha + (uint32_t)hb;
             if (KMAX > 0) {
+              // unconditional stores at the queue's next slot (row qn <= 16 of 17), kept only if counted
               const bool qa = ha && d2a < thr, qb = hb && d2b < thr;
-              if (qa) kq[qn * 32 + lane] = d2a;
+              kq[qn * 32 + lane] = d2a;
               qn += (uint32_t)qa;
-              if (qb) kq[qn * 32 + lane] = d2b;
+              kq[qn * 32 + lane] = d2b;
               qn += (uint32_t)qb;
             }
             if (RDF) {
+              // every lane stores (no branch): a hit at its compacted slot, a miss in the trash row
               const uint32_t ba = __ballot_sync(0xffffffffu, ha);
-              if (ha) wlist[nh + __popc(ba & lt)] = d2a;
+              wlist[ha ? nh + __popc(ba & lt) : 32 * kHalf + lane] = d2a;
               nh += __popc(ba);
               const uint32_t bb = __ballot_sync(0xffffffffu, hb);
-              if (hb) wlist[nh + __popc(bb & lt)] = d2b;
+              wlist[hb ? nh + __popc(bb & lt) : 32 * kHalf + lane] = d2b;
               nh += __popc(bb);
             }
           }
@@ -822,7 +824,7 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
-  __shared__ float2 s_hits[8][32 * kHalf];  // per warp: (d2, weight) of one half-batch's hits
+  __shared__ float2 s_hits[8][32 * kHalf + 32];  // per warp: (d2, weight) of one half-batch's hits + a trash row
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   Hist<true> H;
   H.init(a, smem, 0, true);
@@ -951,11 +953,12 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
               f2_unpack(f2_add(zw.y, pc), wa, wb);
               const bool ha = d2a < emax && wa > 0.f;
               const bool hb = d2b < emax && wb > 0.f;
+              // every lane stores (no branch): a hit at its compacted slot, a miss in the trash row
               const uint32_t ba = __ballot_sync(0xffffffffu, ha);
-              if (ha) wlist[nh + __popc(ba & lt)] = make_float2(d2a, wa);
+              wlist[ha ? nh + __popc(ba & lt) : 32 * kHalf + lane] = make_float2(d2a, wa);
               nh += __popc(ba);
               const uint32_t bb = __ballot_sync(0xffffffffu, hb);
-              if (hb) wlist[nh + __popc(bb & lt)] = make_float2(d2b, wb);
+              wlist[hb ? nh + __popc(bb & lt) : 32 * kHalf + lane] = make_float2(d2b, wb);
               nh += __popc(bb);
             }
             __syncwarp();

@@ -84,3 +84,23 @@ def test_needle_sample_is_the_middle_of_the_needle(orc, spec, monkeypatch):
     assert n_core == off[hi] - off[lo] == len(core)
     got = sum(orc.spatstat(*pt, "all", "all", 0.5, 0.0, 0.01, 100, [1])["n_central"] for pt in parts)
     assert got == int((d[off[lo]:off[hi]] >= 0.5).sum())
+
+
+def test_symmetric_pass_test_count_brute_force():
+    """The symmetric RDF pass tests every unordered pair of records whose cells are within the
+    stencil once: (sum over records of their stencil population - n) / 2, by brute force."""
+    rng = np.random.default_rng(8)
+    n = 2500
+    xyz = (rng.random((n, 3)) * np.array([6.0, 5.0, 7.0])).astype(np.float32)
+    t = rng.integers(0, 2, n).astype(np.uint8)
+    d = np.full(n, np.nan, np.float32)  # no d_srf filter applies to the record count
+    h, stencil = 1.0, 2
+    org = xyz.min(axis=0)
+    dims = tuple(int(np.floor((xyz[:, a].max() - org[a]) / h)) + 1 for a in range(3))
+    info = dict(dims=dims, origin=tuple(float(v) for v in org), cell=h, n_cells=dims[0] * dims[1] * dims[2])
+    full = bench.candidate_tests(torch.from_numpy(xyz), torch.from_numpy(t), torch.from_numpy(d), "all", "all", 0.0,
+                                 info, stencil, all_records=True)
+    c = _cells_np(xyz, org, np.float32(1.0 / h), dims)
+    cheb = np.abs(c[:, None, :] - c[None, :, :]).max(axis=2)
+    pairs = int(np.triu(cheb <= stencil, k=1).sum())
+    assert (full - n) // 2 == pairs and (full - n) % 2 == 0
