@@ -25,6 +25,7 @@
 // insertion).  Counts go to per-CTA shared-memory histograms (the per-thread
 // buffers) added to the uint64 global histograms when the CTA finishes.
 #include <cstring>
+#include <vector>
 
 #include "ps_internal.cuh"
 
@@ -64,6 +65,9 @@ struct QueryArgs {
   uint32_t* next_front;   // work counters of the front (heavy) and back (light) items
   uint32_t* next_light;
   const uint32_t* pfx;    // symmetric RDF pass: central prefix over the neighbour records
+  // bin lookup table (lut_shift = 0: none): cell c covers the float32 bit patterns
+  // [(lut_base + c) << lut_shift, (lut_base + c + 1) << lut_shift), at most one interior edge each
+  uint32_t lut_shift, lut_base, lut_n;
 };
 
 template <int K>
@@ -99,19 +103,23 @@ __device__ __forceinline__ uint32_t bin_index(float d2, const float* sE, uint32_
 }
 
 struct SmemLayout {
-  uint32_t off_E, off_rdf, off_knn, off_kmeta, off_stage, total;
+  uint32_t off_E, off_lut, off_rdf, off_knn, off_kmeta, off_stage, total;
   bool priv;
 };
+
+constexpr uint32_t kLutMax = 4096;  // entries of the bin lookup table (uint16)
 
 constexpr uint32_t kPrivBins = 512;  // up to this many bins each warp keeps its own 32-bit RDF row
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k, bool rdf, uint32_t stage_cap,
-                                                  bool allow_priv = false) {
+                                                  bool allow_priv = false, uint32_t lut_n = 0) {
   SmemLayout L;
   uint32_t o = 0;
   L.priv = allow_priv && rdf && n_bins <= kPrivBins;
   L.off_E = o;
   o += (n_bins + 1) * 4;
+  L.off_lut = o;
+  o += rdf ? lut_n * 2 : 0;
   o = (o + 7u) & ~7u;
   L.off_rdf = o;
   o += rdf ? (L.priv ? 8 * n_bins * 4 : n_bins * 8) : 0;
@@ -135,12 +143,18 @@ struct Hist {
   bool priv;
   uint32_t* s_knn;            // per-CTA central counts stay below n < 2^32
   uint32_t* s_kmeta;
+  uint16_t* lut;              // bin lookup table (see QueryArgs)
+  uint32_t lut_shift, lut_base, lut_last;
   float Emax, E0, r0f, inv_dr;
   uint32_t nb;
 
   __device__ void init(const QueryArgs& a, unsigned char* smem, uint32_t stage_cap, bool allow_priv = false) {
-    const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap, allow_priv);
+    const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap, allow_priv, a.lut_n);
     sE = reinterpret_cast<float*>(smem + L.off_E);
+    lut = reinterpret_cast<uint16_t*>(smem + L.off_lut);
+    lut_shift = RDF ? a.lut_shift : 0u;
+    lut_base = a.lut_base;
+    lut_last = a.lut_n ? a.lut_n - 1 : 0;
     priv = L.priv;
     s_rdf = reinterpret_cast<unsigned long long*>(smem + L.off_rdf);
     s_rdfw = reinterpret_cast<uint32_t*>(smem + L.off_rdf) + (threadIdx.x >> 5) * a.n_bins;
@@ -161,49 +175,64 @@ struct Hist {
     for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x) s_knn[b] = 0;
     for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x) s_kmeta[b] = 0;
     __syncthreads();
+    if (RDF && lut_shift) {
+      // entry c: the largest b < nb with E[b] <= the smallest value of cell c (0 below E[0])
+      for (uint32_t c = threadIdx.x; c < a.lut_n; c += blockDim.x) {
+        const float v = __uint_as_float((lut_base + c) << lut_shift);
+        uint32_t lo = 0, hi = nb;  // invariant: E[lo] <= v or lo == 0; E[hi] > v or hi == nb
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (sE[mid] <= v)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        lut[c] = (uint16_t)lo;
+      }
+      __syncthreads();
+    }
     Emax = sE[nb];
     E0 = sE[0];
     r0f = (float)a.r0;
     inv_dr = (float)(1.0 / a.dr);
   }
 
-  // one in-range pair (d2 < Emax): RDF bin
-  __device__ __forceinline__ void pair(const QueryArgs& a, float d2, uint64_t& binned, uint64_t& below) {
-    if (!RDF) return;
-    if (d2 >= E0) {
-      const uint32_t b = bin_index(d2, sE, nb, r0f, inv_dr);
-      if (priv)
-        atomicAdd(&s_rdfw[b], 1u);
-      else
-        atomicAdd(&s_rdf[b], 1ull);
-      ++binned;
-    } else {
-      ++below;
+  // bin b in [0, nb) with E[b] <= d2 < E[b+1] for E[0] <= d2 < E[nb]: from the lookup table (the
+  // cell of d2's bit pattern holds at most one interior edge, so the bin is the entry or the next
+  // one), else from an approximate square root checked against the edges
+  __device__ __forceinline__ uint32_t bin(float d2) const {
+    if (lut_shift) {
+      // below the first cell (whose start is at most E[1]) the bin is 0
+      const int32_t c = (int32_t)(__float_as_uint(d2) >> lut_shift) - (int32_t)lut_base;
+      const uint32_t b0 = c < 0 ? 0u : lut[(uint32_t)c > lut_last ? lut_last : (uint32_t)c];
+      return b0 + (d2 >= sE[b0 + 1] ? 1u : 0u);
     }
+    return bin_index(d2, sE, nb, r0f, inv_dr);
   }
 
-  // one in-range unordered pair of weight w (the number of its central ends)
-  __device__ __forceinline__ void pair_w(const QueryArgs& a, float d2, uint32_t w, uint64_t& binned, uint64_t& below) {
+  // one in-range pair (d2 < Emax) of weight w: the RDF bin, or the count below E[0].  The pairs
+  // binned are not counted here: the flushes add the rows' sums to the meta array.
+  __device__ __forceinline__ void pair_w(float d2, uint32_t w, uint32_t& below) {
+    if (!RDF) return;
+    const bool in = d2 >= E0;
+    const uint32_t b = bin(in ? d2 : E0);
+    if (priv)
+      atomicAdd(&s_rdfw[b], in ? w : 0u);
+    else
+      atomicAdd(&s_rdf[b], (unsigned long long)(in ? w : 0u));
+    below += in ? 0u : w;
+  }
+  __device__ __forceinline__ void pair(const QueryArgs& a, float d2, uint32_t& below) { pair_w(d2, 1u, below); }
+
+  // one in-range pair of weight w counted straight into the global histogram (and into binned)
+  __device__ __forceinline__ void pair_global(const QueryArgs& a, float d2, uint32_t w, uint64_t& binned,
+                                              uint32_t& below) {
+    if (!RDF) return;
     if (d2 >= E0) {
-      const uint32_t b = bin_index(d2, sE, nb, r0f, inv_dr);
-      if (priv)
-        atomicAdd(&s_rdfw[b], w);
-      else
-        atomicAdd(&s_rdf[b], (unsigned long long)w);
+      atomicAdd((unsigned long long*)&a.rdf[bin(d2)], (unsigned long long)w);
       binned += w;
     } else {
       below += w;
-    }
-  }
-
-  // one in-range pair counted straight into the global histogram
-  __device__ __forceinline__ void pair_global(const QueryArgs& a, float d2, uint64_t& binned, uint64_t& below) {
-    if (!RDF) return;
-    if (d2 >= E0) {
-      atomicAdd((unsigned long long*)&a.rdf[bin_index(d2, sE, nb, r0f, inv_dr)], 1ull);
-      ++binned;
-    } else {
-      ++below;
     }
   }
 
@@ -220,12 +249,21 @@ struct Hist {
     atomicAdd(sp, 1u);
   }
 
-  // one warp adds its private RDF row to the global histogram and clears it
+  // one warp adds its private RDF row to the global histogram (and its sum to the pair count)
+  // and clears it
   __device__ void flush_warp(const QueryArgs& a) {
     if (!RDF || !priv) return;
     __syncwarp();
+    unsigned long long tot = 0;
     for (uint32_t b = threadIdx.x & 31; b < nb; b += 32)
-      if (s_rdfw[b]) atomicAdd((unsigned long long*)&a.rdf[b], (unsigned long long)s_rdfw[b]), s_rdfw[b] = 0;
+      if (s_rdfw[b]) {
+        tot += s_rdfw[b];
+        atomicAdd((unsigned long long*)&a.rdf[b], (unsigned long long)s_rdfw[b]);
+        s_rdfw[b] = 0;
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd((unsigned long long*)&a.meta[PS_META_N_PAIRS], tot);
     __syncwarp();
   }
 
@@ -233,6 +271,7 @@ struct Hist {
   // per-warp rows are summed in the CTA first, one global atomic per bin and CTA
   __device__ void flush(const QueryArgs& a) {
     __syncthreads();
+    unsigned long long tot = 0;  // pairs binned in this CTA's rows
     if (RDF && priv) {
       uint32_t* rows = reinterpret_cast<uint32_t*>(s_rdf);
       const uint32_t nw = blockDim.x >> 5;
@@ -240,11 +279,17 @@ struct Hist {
         unsigned long long sum = 0;
         for (uint32_t w = 0; w < nw; ++w) sum += rows[w * nb + b], rows[w * nb + b] = 0;
         if (sum) atomicAdd((unsigned long long*)&a.rdf[b], sum);
+        tot += sum;
       }
     }
     if (RDF && !priv)
       for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
-        if (s_rdf[b]) atomicAdd((unsigned long long*)&a.rdf[b], s_rdf[b]), s_rdf[b] = 0;
+        if (s_rdf[b]) tot += s_rdf[b], atomicAdd((unsigned long long*)&a.rdf[b], s_rdf[b]), s_rdf[b] = 0;
+    if (RDF) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd((unsigned long long*)&a.meta[PS_META_N_PAIRS], tot);
+    }
     for (uint32_t b = threadIdx.x; b < a.n_k * nb; b += blockDim.x)
       if (s_knn[b]) atomicAdd((unsigned long long*)&a.knn[b], (unsigned long long)s_knn[b]), s_knn[b] = 0;
     for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x)
@@ -257,6 +302,8 @@ struct Hist {
 // pair counters of the whole CTA (every thread calls it): summed in the warp, then in shared
 // memory, one global atomic per counter and CTA
 __device__ __forceinline__ void add_pair_counters(const QueryArgs& a, uint64_t binned, uint64_t below) {
+  // binned: only the pairs counted straight into the global histogram (the shared rows' pairs
+  // are added by the flushes); below: pairs with d2 < E[0]
   __shared__ unsigned long long s_pc[2];
   if (threadIdx.x == 0) s_pc[0] = 0, s_pc[1] = 0;
 #pragma unroll
@@ -335,7 +382,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   const uint32_t n_hi = a.cgeo->work_n4, n_front = n_hi + a.cgeo->work_n2, n_light = a.cgeo->work_n3;
   const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   const float erange = a.emax_near > 0.f ? a.emax_near : H.Emax;  // squared search range of this pass
-  uint64_t my_binned = 0, my_below = 0;
+  uint64_t my_binned = 0;  // pairs counted straight into the global histogram
+  uint32_t my_below = 0;   // pairs below E[0]
   float4* buf = s_buf[w];
   float* wlist = s_hits[w];
   float* kq = s_kq[w];
@@ -455,7 +503,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
           if (RDF) {
             __syncwarp();
-            for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], my_binned, my_below);
+            for (uint32_t h = lane; h < nh; h += 32) H.pair(a, wlist[h], my_below);
             __syncwarp();
             wcount += nh;
             if (wcount >= (1ull << 31)) {
@@ -519,7 +567,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
           if (d2 < erange && __float_as_uint(q.w) != pidx) {
             ++within;
-            H.pair(a, d2, my_binned, my_below);
+            H.pair(a, d2, my_below);
             if (KMAX > 0) topk_insert(top, d2);
           }
         }
@@ -617,9 +665,9 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
                 ++within;
                 if (RDF) {
                   if (within <= kRowLaneCap)
-                    H.pair(a, d2, my_binned, my_below);
+                    H.pair(a, d2, my_below);
                   else
-                    H.pair_global(a, d2, my_binned, my_below);
+                    H.pair_global(a, d2, 1u, my_binned, my_below);
                 }
                 if (KMAX > 0 && d2 < top[KK - 1]) topk_insert(top, d2);
               }
@@ -670,13 +718,15 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
     s_timeout = 0;
   }
   H.init(a, smem, a.stage_cap);
-  float4* s_cand = reinterpret_cast<float4*>(smem + smem_layout(a.n_bins, a.n_k, RDF, a.stage_cap).off_stage);
+  float4* s_cand =
+      reinterpret_cast<float4*>(smem + smem_layout(a.n_bins, a.n_k, RDF, a.stage_cap, false, a.lut_n).off_stage);
   const uint32_t tid = threadIdx.x;
   const Geo ng = *a.ngeo;
   const uint32_t work_n = a.cgeo->work_n;
   const uint32_t n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
   uint32_t phase = 0, stuck_phase = 0;
-  uint64_t my_binned = 0, my_below = 0;
+  uint64_t my_binned = 0;
+  uint32_t my_below = 0;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(&a.cgeo->work_next, 1u);
@@ -740,7 +790,7 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
               const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
               if (d2 < H.Emax && __float_as_uint(q.w) != pidx) {
                 ++within;
-                H.pair(a, d2, my_binned, my_below);
+                H.pair(a, d2, my_below);
                 if (KMAX > 0) topk_insert(top, d2);
               }
             }
@@ -824,7 +874,8 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
-  __shared__ float2 s_hits[8][32 * kHalf + 32];  // per warp: (d2, weight) of one half-batch's hits + a trash row
+  __shared__ uint32_t s_hits[8][32 * kHalf + 32];  // per warp: one half-batch's hits + a trash row: the bits
+                                                  // of d2, the sign bit set for weight 2
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   Hist<true> H;
   H.init(a, smem, 0, true);
@@ -834,9 +885,10 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   const Geo ng = *a.ngeo;
   const uint32_t n_cells = ng.n_cells;
   const int s = a.stencil, n_runs = (2 * s + 1) * s + s + 1;
-  uint64_t my_binned = 0, my_below = 0;
+  uint64_t my_binned = 0;
+  uint32_t my_below = 0;
   float* bf = reinterpret_cast<float*>(s_buf[w]);
-  float2* wlist = s_hits[w];
+  uint32_t* wlist = s_hits[w];
   uint32_t* rsrc = s_rsrc[w];
   uint32_t* rpre = s_rpre[w];
   const float E_max = H.Emax;
@@ -876,26 +928,29 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
       if (lane == 0) rpre[0] = 0;
       __syncwarp();
 
-      // candidate at virtual position pos (runs concatenated), its central flag in .w
+      // candidate at virtual position pos (runs concatenated); .w = E[nb] for a central, -1 otherwise
       auto fetch = [&](uint32_t pos, int& rr) -> float4 {
-        if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, -1.f);
         while (pos >= rpre[rr + 1]) ++rr;
         const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
         float4 q = __ldg(a.nrec + j);
-        q.w = (float)(__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+        q.w = __ldg(a.pfx + j + 1) > __ldg(a.pfx + j) ? E_max : -1.f;
         return q;
       };
 
       for (uint32_t i0 = a0; i0 < a1; i0 += 32) {
         const uint32_t i = i0 + lane;
         const bool valid = i < a1;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 p = make_float4(INFINITY, INFINITY, INFINITY, 0.f);  // lanes without a record never hit
         float ci = 0.f;
         if (valid) {
           p = __ldg(a.nrec + i);
           ci = (float)(__ldg(a.pfx + i + 1) - __ldg(a.pfx + i));
         }
-        const float emax = valid ? E_max : -INFINITY;
+        // a pair counts when either end is central: the range is max(lane's, candidate's), each
+        // E[nb] for a central and -1 otherwise; weight 2 (sign bit) when both are
+        const float elane = ci > 0.f ? E_max : -1.f;
+        const uint32_t w2lane = ci > 0.f ? 0x80000000u : 0u;
         // pairs inside the cell: j in (i, a1), each lane on its own (a small share of the pairs)
         {
           uint32_t inc = 0;
@@ -907,13 +962,9 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
               const uint32_t wt = (uint32_t)ci + (__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
               if (d2 < E_max && wt) {
                 if (big) {
-                  if (d2 >= H.E0)
-                    atomicAdd((unsigned long long*)&a.rdf[bin_index(d2, H.sE, H.nb, H.r0f, H.inv_dr)],
-                              (unsigned long long)wt), my_binned += wt;
-                  else
-                    my_below += wt;
+                  H.pair_global(a, d2, wt, my_binned, my_below);
                 } else {
-                  H.pair_w(a, d2, wt, my_binned, my_below);
+                  H.pair_w(d2, wt, my_below);
                   inc += wt;
                 }
               }
@@ -928,7 +979,6 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
         // the half stencil: 32 candidates per coalesced load, staged as 16 interleaved pairs
         // (xa xb ya yb za zb ca cb), tested two at a time
         const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
-        const unsigned long long pc = f2_pack(ci, ci);
         int rr = 0;
         float4 nxt = fetch(lane, rr);
         for (uint32_t b = 0; b < n_cand; b += 32) {
@@ -949,22 +999,24 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
               const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
               float d2a, d2b;
               dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
-              float wa, wb;
-              f2_unpack(f2_add(zw.y, pc), wa, wb);
-              const bool ha = d2a < emax && wa > 0.f;
-              const bool hb = d2b < emax && wb > 0.f;
+              float ea, eb;
+              f2_unpack(zw.y, ea, eb);
+              const bool ha = d2a < fmaxf(elane, ea);
+              const bool hb = d2b < fmaxf(elane, eb);
+              const uint32_t va = __float_as_uint(d2a) | (~__float_as_uint(ea) & w2lane);
+              const uint32_t vb = __float_as_uint(d2b) | (~__float_as_uint(eb) & w2lane);
               // every lane stores (no branch): a hit at its compacted slot, a miss in the trash row
               const uint32_t ba = __ballot_sync(0xffffffffu, ha);
-              wlist[ha ? nh + __popc(ba & lt) : 32 * kHalf + lane] = make_float2(d2a, wa);
+              wlist[ha ? nh + __popc(ba & lt) : 32 * kHalf + lane] = va;
               nh += __popc(ba);
               const uint32_t bb = __ballot_sync(0xffffffffu, hb);
-              wlist[hb ? nh + __popc(bb & lt) : 32 * kHalf + lane] = make_float2(d2b, wb);
+              wlist[hb ? nh + __popc(bb & lt) : 32 * kHalf + lane] = vb;
               nh += __popc(bb);
             }
             __syncwarp();
             for (uint32_t h = lane; h < nh; h += 32) {
-              const float2 e = wlist[h];
-              H.pair_w(a, e.x, (uint32_t)e.y, my_binned, my_below);
+              const uint32_t v = wlist[h];
+              H.pair_w(__uint_as_float(v & 0x7FFFFFFFu), 1u + (v >> 31), my_below);
             }
             __syncwarp();
             wcount += 2ull * nh;
@@ -1028,6 +1080,34 @@ static int dispatch_k(const ps_grid* g, const QueryArgs& qa, uint32_t sc, uint32
   return launch_query<32, RDF>(g, qa, sc, sw, s);
 }
 
+// Parameters of the bin lookup table: the largest bit shift S at which the interior edges
+// E[1..nb-1] fall in strictly increasing cells of the float32 bit pattern (bits >> S), so that a
+// cell holds at most one edge; the table covers the cells from E[1]'s to E[nb]'s.  None when the
+// table would exceed kLutMax entries or two edges coincide.
+static void choose_lut(ps_bins bins, QueryArgs& qa) {
+  qa.lut_shift = qa.lut_base = qa.lut_n = 0;
+  const uint32_t nb = bins.n_bins;
+  if (nb < 2) return;
+  std::vector<uint32_t> Eb(nb + 1);
+  for (uint32_t b = 0; b <= nb; ++b) {
+    const double e = bins.r0 + (double)b * bins.dr;
+    const float f = (float)(e * e);
+    memcpy(&Eb[b], &f, 4);
+  }
+  for (int S = 30; S >= 1; --S) {
+    bool ok = true;
+    for (uint32_t b = 2; b < nb && ok; ++b) ok = (Eb[b] >> S) > (Eb[b - 1] >> S);
+    if (!ok) continue;
+    const uint32_t base = Eb[1] >> S, n = (Eb[nb] >> S) - base + 1;
+    if (n <= kLutMax) {
+      qa.lut_shift = (uint32_t)S;
+      qa.lut_base = base;
+      qa.lut_n = n;
+    }
+    return;  // the largest separating shift gives the smallest table
+  }
+}
+
 int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
               const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
               uint32_t* d_nwithin, cudaStream_t s) {
@@ -1061,6 +1141,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.n = g->n;
   qa.next_front = &g->ctr.geo->work_next2;
   qa.next_light = &g->ctr.geo->work_next3;
+  choose_lut(bins, qa);
 
   const bool rdf = d_rdf != nullptr;
   ZeroOut z;  // the outputs are zeroed by the central-list reset kernel
@@ -1075,14 +1156,14 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   // staging budget of the CTA kernel: two CTAs per SM
   int dev_smem = 0;
   PS_CUDA(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
-  const SmemLayout base = smem_layout(bins.n_bins, n_k, rdf, 0);
+  const SmemLayout base = smem_layout(bins.n_bins, n_k, rdf, 0, false, qa.lut_n);
   const uint32_t budget = (uint32_t)dev_smem / 2 - 2048;
   if (base.total + 16 * 1024 > (uint32_t)dev_smem - 1024)
     return fail(PS_ERR_UNSUPPORTED, "too many bins x k values for shared memory");
   uint32_t stage_bytes = budget > base.total + 16 * 1024 ? budget - base.total : 16 * 1024;
   qa.stage_cap = (stage_bytes / 16) & ~7u;
-  const uint32_t smem_cta = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap).total;
-  const uint32_t smem_warp = smem_layout(bins.n_bins, n_k, rdf, 0, true).total;
+  const uint32_t smem_cta = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap, false, qa.lut_n).total;
+  const uint32_t smem_warp = smem_layout(bins.n_bins, n_k, rdf, 0, true, qa.lut_n).total;
   bool subset = !g->pack_type;
   for (int w = 0; w < 4; ++w) subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
   if (g->split && subset && rdf && d_nwithin == nullptr && g->stencil == 2 && g->dense_min == 0xFFFFFFFFu) {
@@ -1110,7 +1191,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
     QueryArgs qs = qa;
     qs.n_k = 0;
     qs.pfx = reinterpret_cast<const uint32_t*>(g->cr);  // written by the central-list compaction
-    const uint32_t smem_sym = smem_layout(bins.n_bins, 0, true, 0, true).total;
+    const uint32_t smem_sym = smem_layout(bins.n_bins, 0, true, 0, true, qa.lut_n).total;
     PS_CUDA(cudaFuncSetAttribute(k_rdf_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sym));
     int per_sm = 0;
     PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rdf_sym, 256, smem_sym));

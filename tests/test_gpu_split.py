@@ -122,3 +122,17 @@ def test_split_edge_cases(ps, orc, spec):
         r = orc.spatstat(xyz, t, d, "all", "all", 0.2, *bins, ks)
         assert_same({k: v.cpu().numpy() for k, v in o.items() if v is not None}, r, ks)
     grid.close()
+
+
+@pytest.mark.parametrize("bins", [(0.0, 0.01, 200), (0.0, 0.001, 2000), (0.5, 0.005, 300), (0.0, 0.25, 8),
+                                  (0.0, 2.0, 1)])
+def test_bin_lookup_regimes(ps, orc, spec, bins):
+    """The bin of a pair comes from a lookup table on the float32 bit pattern of d2 where the
+    edges are far enough apart (one interior edge per table cell), else from an approximate
+    square root checked against the edges: fine bins (no table), r0 > 0, a few wide bins and a
+    single bin, in both query forms."""
+    xyz, t, d = spec.cube(207, 6000, 6.0, (0.7, 0.3))
+    r = orc.spatstat(xyz, t, d, "all", "all", 0.5, *bins, [1, 4], per_central=True)
+    for split in (False, True):
+        g = run_gpu(ps, xyz, t, d, "all", "all", 0.5, bins, [1, 4], per_central="kth", cell_scale=0.5, split=split)
+        assert_same(g, r, [1, 4], per_central="kth")
