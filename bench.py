@@ -59,6 +59,10 @@ WORKLOADS = {
         desc="needle 8.07e6 ions (r_tip 20 nm, 10 deg, h 100 nm, 30/nm^3, Al3Sc precipitates); Sc-Sc + Si-Si; "
              "kNN k=1,5,10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
         combos=[("Sc-Sc", [1], [1]), ("Si-Si", [2], [2])], ks=[1, 5, 10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
+    "needle8m-allall": dict(
+        desc="needle 8.07e6 ions (r_tip 20 nm, 10 deg, h 100 nm, 30/nm^3, Al3Sc precipitates); all-all; "
+             "kNN k=10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
+        combos=[("all-all", "all", "all")], ks=[10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0),
     "cylinder200k": dict(
         desc="Poisson cylinder 2e5 ions (R 10 nm, H 15.9 nm, 40/nm^3); all-all; kNN k=1 + RDF r=[0,0.01,2] nm; "
              "d_srf>=1 nm",
@@ -70,7 +74,7 @@ SECONDARY = ("needle8m", "cylinder200k")
 def make_cloud(name: str, seed_offset: int = 0):
     from paper_2004_05188_gb300 import specimen
 
-    if name == "needle8m":
+    if name in ("needle8m", "needle8m-allall"):
         return specimen.needle(specimen.needle_8m_params(seed=2 + seed_offset))
     if name == "cylinder200k":
         return specimen.cylinder_small(seed=1 + seed_offset)
@@ -819,7 +823,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
                  "timings_ms": None}
     else:
         tuned = autotune.tune(X[a:b], T[a:b], D[a:b], nbr0, ctr0, wl["dsrf_min"], bins, wl["ks"],
-                              candidates=((1.0, 0), (0.5, 0), (0.5, 0, 1)), reps=2)
+                              candidates=((1.0, 0), (0.5, 0), (0.5, 0, 1), (1.0, 128)), reps=2)
     cs, dm, sp = tuned["cell_scale"], tuned["dense_min"], int(tuned.get("split", 0))
     # the other combinations keep the cell size (one grid) and tune only the query options
     qopts = {name0: (dm, sp)}
@@ -832,6 +836,10 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
                            candidates=((cs, 0, 0), (cs, 0, 1)), reps=2)
         qopts[name] = (int(t2["dense_min"]), int(t2.get("split", 0)))
         tunings[name] = t2.get("timings_ms")
+    if dist is not None:  # every rank uses rank 0's choice (results do not depend on it; timings would)
+        pick = [(cs, dm, sp, qopts, tunings)]
+        dist.broadcast_object_list(pick, src=0)
+        cs, dm, sp, qopts, tunings = pick[0]
     grid = ps.Grid(N, cs, dm, bool(sp))
     nk = len(wl["ks"])
     outs = [dict(rdf=torch.empty(bins[2], dtype=torch.int64, device=dev),
@@ -1118,7 +1126,7 @@ def run_gpu(args, wl_name, wl):
             w2 = resolve(name)
             r = measure_replica(args, name, w2, dev, None, 1, 0, peaks, 20, 5, False)
             secondary[name] = {k: r[k] for k in ("workload", "value", "ms_per_step", "steps", "n_queries",
-                                                 "neighbour_pairs_per_s", "kernel_config", "clocks")}
+                                                 "neighbour_pairs_per_s", "kernel_config", "autotune", "clocks")}
             secondary[name]["roofline"] = {k: r["roofline"][k] for k in ("achieved", "peak", "unit", "frac", "traffic",
                                                                          "avg_launch_ms", "time_share")}
             secondary[name]["smem_atomic_frac"] = r["roofline"]["smem_atomic"]["frac"]

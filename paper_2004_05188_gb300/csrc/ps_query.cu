@@ -939,8 +939,14 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
       };
 
       for (uint32_t i0 = a0; i0 < a1; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        const bool valid = i < a1;
+        // L lanes per record when the chunk holds few records (a cell's last chunk, sparse cells):
+        // lane sub of a record tests the candidate pairs t = sub mod L
+        const uint32_t m = min(32u, a1 - i0);
+        const uint32_t L = item_lanes(m < 4u ? 4u : m);
+        const uint32_t lg = L == 8u ? 3u : (L == 4u ? 2u : (L == 2u ? 1u : 0u));
+        const uint32_t sub = lane & (L - 1u), n_it = 8u >> lg;
+        const uint32_t i = i0 + (lane >> lg);
+        const bool valid = (lane >> lg) < m;
         float4 p = make_float4(INFINITY, INFINITY, INFINITY, 0.f);  // lanes without a record never hit
         float ci = 0.f;
         if (valid) {
@@ -956,7 +962,7 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
           uint32_t inc = 0;
           if (valid) {
             const bool big = a1 - a0 > (1u << 20);  // per-lane increments stay far below the row's 2^32
-            for (uint32_t j = i + 1; j < a1; ++j) {
+            for (uint32_t j = i + 1 + sub; j < a1; j += L) {
               const float4 q = __ldg(a.nrec + j);
               const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
               const uint32_t wt = (uint32_t)ci + (__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
@@ -993,8 +999,8 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
           for (int half = 0; half < 2; ++half) {
             uint32_t nh = 0;  // hits in the warp list (uniform)
 #pragma unroll 2
-            for (uint32_t u = 0; u < 8; ++u) {
-              const uint32_t t = 8 * half + u;
+            for (uint32_t u = 0; u < n_it; ++u) {
+              const uint32_t t = 8 * half + u * L + sub;
               const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
               const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
               float d2a, d2b;

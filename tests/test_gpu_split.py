@@ -136,3 +136,17 @@ def test_bin_lookup_regimes(ps, orc, spec, bins):
     for split in (False, True):
         g = run_gpu(ps, xyz, t, d, "all", "all", 0.5, bins, [1, 4], per_central="kth", cell_scale=0.5, split=split)
         assert_same(g, r, [1, 4], per_central="kth")
+
+
+@pytest.mark.parametrize("rho", [3.0, 12.0, 33.0])
+def test_split_lane_chunks(ps, orc, spec, rho):
+    """Chunks of few records (sparse cells, a cell's last chunk past 32 records) give several
+    lanes to a record: 3, 12 and 33 ions per nm^3 on cells of ~1 nm^3 cover 8, 4, 2 and 1 lanes
+    per record."""
+    L = 9.0
+    xyz, t, d = spec.cube(208, int(rho * L**3), L, (0.6, 0.4))
+    bins = (0.0, 0.02, 100)
+    for ctr, nbr, ks in (("all", "all", [1, 6]), ([1], [0, 1], [2]), ([0], [0], [])):
+        r = orc.spatstat(xyz, t, d, ctr, nbr, 0.7, *bins, ks, per_central=True)
+        g = run_gpu(ps, xyz, t, d, ctr, nbr, 0.7, bins, ks, per_central="kth", cell_scale=0.5, split=True)
+        assert_same(g, r, ks, per_central="kth")
