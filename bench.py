@@ -55,6 +55,11 @@ WORKLOADS = {
              "kNN k=10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
         combos=[("all-all", "all", "all"), ("Sc-Sc", [1], [1])], ks=[10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0,
         sharded=True),
+    "needle200m": dict(
+        desc="needle 2e8 ions (r_tip 40 nm, 15 deg, height for 2e8 ions, 30/nm^3, Al3Sc precipitates); all-all + Sc-Sc; "
+             "kNN k=10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
+        combos=[("all-all", "all", "all"), ("Sc-Sc", [1], [1])], ks=[10], spec=(0.0, 0.01, 2.0), dsrf_min=2.0,
+        sharded=True),
     "needle8m": dict(
         desc="needle 8.07e6 ions (r_tip 20 nm, 10 deg, h 100 nm, 30/nm^3, Al3Sc precipitates); Sc-Sc + Si-Si; "
              "kNN k=1,5,10 + RDF r=[0,0.01,2] nm; d_srf>=2 nm",
@@ -86,6 +91,8 @@ def needle_params(name: str):
 
     if name == "needle2g":
         return specimen.needle_2g_params()
+    if name == "needle200m":
+        return specimen.needle_params(40.0, 15.0, specimen.height_for(2e8, 40.0, 15.0), seed=6)
     raise ValueError(name)
 
 
@@ -117,8 +124,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_traffic.json")
 
 
 def stored_traffic(workload: str, kernel_config: dict):
-    """DRAM bytes per query launch from the stored ncu record (profiles/query_traffic.json), or None
-    when no record was taken on these kernel sources, this workload and this kernel configuration."""
+    """DRAM bytes per launch of the query kernels from the stored ncu record
+    (profiles/query_traffic.json): {"combination": name, "kernels": {family: bytes}}, or None when
+    no record was taken on these kernel sources, this workload and this kernel configuration."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
@@ -126,7 +134,9 @@ def stored_traffic(workload: str, kernel_config: dict):
     for rec in recs:
         if (rec.get("workload") == workload and rec.get("source_sha256") == query_sources_sha256()
                 and rec.get("kernel_config") == kernel_config):
-            return float(rec["dram_bytes_per_launch"])
+            return {"combination": rec["combination"],
+                    "kernels": {k: float(v["dram_bytes_read"] + v["dram_bytes_write"])
+                                for k, v in rec["kernels"].items()}}
     return None
 
 
@@ -409,8 +419,11 @@ def measure_soft(args, dev):
     pert = (xyz + np.random.default_rng(1).normal(0.0, 0.02, xyz.shape)).astype(np.float32)
     Xp = torch.from_numpy(pert).to(dev)
     rc = ps.soft_r_cut(bins, sigma, 1.0)
-    g = ps.Grid(N)
-    gp = ps.Grid(N)
+    # the smoothed form's cell size (--soft-cell-scale); the plain exact RDF on half-size cells in passes
+    # (its fastest form)
+    g = ps.Grid(N, args.soft_cell_scale)
+    gp = ps.Grid(N, args.soft_cell_scale)
+    gplain = ps.Grid(N, 0.5, 0, True)
     # normalisation at fixed density (the library's g(r) finalisation, ps_rdf_normalise):
     # g_b = h_b * factor_b, factor_b = 1 / (N_c (N / V) 4/3 pi (e_{b+1}^3 - e_b^3))
     vol = specimen.frustum_volume(p.r_top, math.degrees(p.half_angle), p.height)
@@ -434,8 +447,8 @@ def measure_soft(args, dev):
         return ps.soft_rdf_bwd(g, D, "all", dmin, sigma, 1.0, bins, G)
 
     def plain():
-        g.build(X, T, "all", 2.0)
-        ps.spatstat(g, D, "all", dmin, bins, [], rdf=True, out=plain_out, check=False)
+        gplain.build(X, T, "all", 2.0)
+        ps.spatstat(gplain, D, "all", dmin, bins, [], rdf=True, out=plain_out, check=False)
 
     for _ in range(2):
         G = loss_grad(fwd())
@@ -460,11 +473,14 @@ def measure_soft(args, dev):
     n_pairs = int(plain_out["meta"][1].item())
     g.close()
     gp.close()
+    gplain.close()
     return {"workload": f"needle {N} ions (1e7 target), all-all, sigma=0.05 nm, r=[0,0.02,2] nm, d_srf>=2.3 nm",
             "n_central": int(n_c), "fwd_ms": f_ms, "bwd_ms": b_ms, "fwd_bwd_ms": f_ms + b_ms,
             "plain_exact_rdf_ms": p_ms, "fwd_bwd_over_plain": (f_ms + b_ms) / p_ms,
             "plain_pairs_per_s": n_pairs / (p_ms * 1e-3), "reps": reps,
-            "timing": "CUDA events, eager, grid build included in fwd and plain"}
+            "cell_scale": args.soft_cell_scale,
+            "timing": "CUDA events, eager, grid build included in fwd and plain; the plain exact RDF on half-size cells "
+                      "in passes (its fastest form)"}
 
 
 def measure_sdm(args, dev):
@@ -667,11 +683,16 @@ QUERY_FAMS = ("query", "knn_full", "rdf_sym")  # the pair tests: one pass, or th
 BUILD_FAMS = ("select", "geometry", "count", "scan", "scatter", "central")
 
 
+KERNEL_NAMES = {"query": "k_query_warp (one pass, or the near-radius kNN pass)",
+                "knn_full": "k_query_warp (full-radius kNN fallback)", "rdf_sym": "k_rdf_sym (RDF over unordered pairs)"}
+
+
 def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
-    """Roofline figures of one measurement: the query against the measured FP32 add/multiply
-    throughput (its bound) and against the measured shared-atomic rate (its RDF increments), and
-    the build kernels against the measured HBM copy bandwidth.  prof: {family: (launches, ms)}
-    summed over `steps` steps; st: per-step counts of every combination."""
+    """Roofline figures of one measurement: the dominant query kernel (by time) against the
+    measured FP32 add/multiply throughput (its bound), every query pass the same way, the query
+    against the measured shared-atomic rate (its RDF increments), and the build kernels against the
+    measured HBM copy bandwidth.  prof: {family: (launches, ms)} summed over `steps` steps; st:
+    per-step counts of every combination; traffic: stored_traffic(...) or None."""
     q_n = sum(prof[f][0] for f in QUERY_FAMS)
     q_ms = sum(prof[f][1] for f in QUERY_FAMS)
     cands = sum(c["candidates"] for c in st["combos"]) * steps
@@ -683,18 +704,50 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
     b_bytes = sum(algorithmic_bytes(f, st, c) for f in BUILD_FAMS for c in st["combos"]) * steps
     b_ms = sum(prof[f][1] for f in BUILD_FAMS)
     tot_ms = sum(v[1] for v in prof.values())
+
+    def launching(fam):  # the combinations that launch this family's kernel once per step
+        if fam == "query":
+            return [c["name"] for c in st["combos"]]
+        return [c["name"] for c in st["combos"] if c.get("split")]
+
+    by_kernel = {}
+    for fam in QUERY_FAMS:
+        n, ms = prof[fam]
+        if n == 0:
+            continue
+        tests = None if fam == "knn_full" else sum(c.get("candidates_by_pass", {}).get(fam, 0)
+                                                     for c in st["combos"]) * steps
+        tf = FLOPS_PER_CANDIDATE * tests / (ms * 1e-3) / 1e12 if tests is not None and ms > 0 else None
+        rec = traffic["kernels"].get(fam) if traffic else None
+        only_rec = traffic is not None and launching(fam) == [traffic["combination"]]
+        by_kernel[fam] = {
+            "kernel": KERNEL_NAMES[fam], "launches": n, "avg_launch_ms": ms / n,
+            "flops_per_launch": FLOPS_PER_CANDIDATE * tests / n if tests is not None else None,
+            "achieved_tflops": tf, "frac": tf / alu_peak if tf is not None and alu_peak > 0 else None,
+            "traffic": rec if only_rec else None,
+            "traffic_per_launch_of": (traffic["combination"] if rec is not None else None),
+            "traffic_recorded": rec}
+    dom = max(by_kernel, key=lambda f: prof[f][1]) if by_kernel else "query"
+    d = by_kernel.get(dom, {})
     return {
-        "bound": "alu", "kernel": "query: k_query_warp (one pass, or near kNN + full-radius fallback) and k_rdf_sym",
-        "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
-        "frac": alu / alu_peak if alu_peak > 0 else None,
+        "bound": "alu", "kernel": KERNEL_NAMES[dom], "family": dom,
+        "achieved": d.get("achieved_tflops") or 0.0, "peak": alu_peak, "unit": "TFLOP/s", "frac": d.get("frac"),
         "peak_source": f"measured: ps_measure_peaks FP32 add/multiply, {peaks['num_sms']} SMs at "
                        f"{peaks['sm_mhz']:.0f} MHz (scalar {peaks['fp32_scalar_gops']:.0f}, packed f32x2 "
                        f"{peaks['fp32_packed_gops']:.0f} Gop/s; the larger is the peak)",
-        "traffic": traffic, "traffic_note": "DRAM bytes per query launch, stored ncu record (profiles/query_traffic.json) "
-                                            "for these kernel sources and this configuration; null if none",
+        "traffic": d.get("traffic"),
+        "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the "
+                        "stored ncu record (profiles/query_traffic.json) for these kernel sources, this workload "
+                        "and this configuration; null if none",
+        "algorithmic_bytes_per_launch": (algorithmic_bytes("query", st, next(c for c in st["combos"]
+                                                                            if c["name"] == traffic["combination"]))
+                                         if traffic and d.get("traffic") else None),
         "per_unit": f"{FLOPS_PER_CANDIDATE} FP32 operations per candidate test (3 sub, 3 mul, 2 add, 1 compare)",
-        "candidate_tests_per_step": cands // max(1, steps), "flops_per_launch": FLOPS_PER_CANDIDATE * cands / max(1, q_n),
-        "launches": q_n, "avg_launch_ms": q_ms / max(1, q_n),
+        "flops_per_launch": d.get("flops_per_launch"), "launches": d.get("launches"),
+        "avg_launch_ms": d.get("avg_launch_ms"),
+        "by_kernel": by_kernel,
+        "all_query_passes": {"achieved": alu, "frac": alu / alu_peak if alu_peak > 0 else None, "launches": q_n,
+                             "avg_launch_ms": q_ms / max(1, q_n), "candidate_tests_per_step": cands // max(1, steps)},
         "pass_ms_per_step": {f: prof[f][1] / max(1, steps) for f in QUERY_FAMS},
         "timing": "CUDA events around every launch on the launching stream, inside the timed region",
         "time_share": q_ms / tot_ms if tot_ms > 0 else None,
@@ -729,12 +782,15 @@ def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil, split=Fa
     if split and subset and stencil == 2:
         near = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, 1) if wl["ks"] else 0
         full = candidate_tests(X, T, D, nbr, nbr, wl["dsrf_min"], info, 2, all_records=True)
-        cands = near + (full - info["n_nbr"]) // 2
+        sym = (full - info["n_nbr"]) // 2
+        by_pass = {"query": near, "rdf_sym": sym}
+        cands = near + sym
     else:
         cands = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil)
+        by_pass = {"query": cands}
     return dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
                 n_ctr_typed=n_typed, n_pairs_local=int(meta[1]), subset=subset, candidates=cands,
-                split=bool(split and subset and stencil == 2))
+                candidates_by_pass=by_pass, split=bool(split and subset and stencil == 2))
 
 
 def e2e_runner(dev, stream, sets, hosts, step, outs, res_h):
@@ -871,7 +927,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
     n_pairs = sum(int(o["meta"][1].item()) for o in outs)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    sampler = ClockSampler(gpu_index(local_rank()), args.clocks_csv)
+    sampler = ClockSampler(gpu_index(dev.index), args.clocks_csv if rank == 0 else None)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ps.prof_enable(FAMS)
@@ -918,6 +974,12 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
     hbm_peak, hbm_src = load_hbm_peak()
     kcfg = {name: {"cell_scale": float(cs), "dense_min": int(qopts[name][0]), "split": int(qopts[name][1])}
             for name, _, _ in wl["combos"]}
+    import hashlib
+
+    dig = hashlib.sha256()
+    for o in outs:  # the whole specimen's histograms and counters (after the combine)
+        for k in ("rdf", "knn", "meta"):
+            dig.update(o[k].cpu().numpy().tobytes())
     roof = rooflines(prof, st, args.steps, peaks, hbm_peak, hbm_src, stored_traffic(wl_name, kcfg))
     grid.close()
     res = {"value": value, "T_ms": T_ms, "n_queries": n_queries, "n_pairs": n_pairs, "launches": launches,
@@ -925,7 +987,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
            "kernel_config": kcfg, "autotune": tunings, "generation_s": gen_s,
            "slab": {"layers": [int(cuts[rank]), int(cuts[rank + 1])], "halo_layers": halo, "ions_generated": N,
                     "core_ions": int(core[1] - core[0])},
-           "step_ms_min_max": [min(step_ms), max(step_ms)]}
+           "step_ms_min_max": [min(step_ms), max(step_ms)], "result_sha256": dig.hexdigest()}
     del X, T, D, pinned, Xh, Th, Dh
     torch.cuda.empty_cache()
     return res
@@ -1010,7 +1072,7 @@ def measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, steps, war
     for _ in range(3):
         graph.replay()
     torch.cuda.synchronize()
-    sampler = ClockSampler(gpu_index(local_rank()), None)
+    sampler = ClockSampler(gpu_index(dev.index), None)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     sampler.start()
@@ -1068,6 +1130,8 @@ def rank_reduce(dist, device, t_max, sums):
 
     if dist is None:
         return float(t_max), [float(x) for x in sums]
+    if dist.get_backend() == "gloo":
+        device = "cpu"
     tt = torch.tensor([float(t_max)], dtype=torch.float64, device=device)
     dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     ss = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
@@ -1085,9 +1149,11 @@ def local_rank() -> int:
 
 
 def gpu_index(local: int) -> int:
+    """nvidia-smi index of the GPU this rank uses (ranks that share a GPU share its index)."""
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
-        return int(vis.split(",")[local])
+        ids = vis.split(",")
+        return int(ids[local % len(ids)])
     return local
 
 
@@ -1098,13 +1164,19 @@ def run_gpu(args, wl_name, wl):
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    local = local_rank()
+    local = local_rank() % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # NCCL, one GPU per rank; PS_BENCH_BACKEND=gloo combines through the host instead (ranks
+        # that share a GPU: every rank's kernels are its own, only the host-side sum joins them)
+        backend = os.environ.get("PS_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     dev = torch.device("cuda", local)
     peaks = ps.measure_peaks()
 
@@ -1127,8 +1199,9 @@ def run_gpu(args, wl_name, wl):
             r = measure_replica(args, name, w2, dev, None, 1, 0, peaks, 20, 5, False)
             secondary[name] = {k: r[k] for k in ("workload", "value", "ms_per_step", "steps", "n_queries",
                                                  "neighbour_pairs_per_s", "kernel_config", "autotune", "clocks")}
-            secondary[name]["roofline"] = {k: r["roofline"][k] for k in ("achieved", "peak", "unit", "frac", "traffic",
-                                                                         "avg_launch_ms", "time_share")}
+            secondary[name]["roofline"] = {k: r["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac",
+                                                                         "traffic", "avg_launch_ms", "time_share")}
+            secondary[name]["roofline"]["all_query_passes_frac"] = r["roofline"]["all_query_passes"]["frac"]
             secondary[name]["smem_atomic_frac"] = r["roofline"]["smem_atomic"]["frac"]
             secondary[name]["hbm_build_frac"] = r["roofline"]["hbm_build"]["frac"]
 
@@ -1171,7 +1244,7 @@ def run_gpu(args, wl_name, wl):
             "gpu_launches_per_step": head["launches"] / args.steps, "clocks": head["clocks"],
             "measured_peaks": peaks, "secondary": secondary, "forms": forms,
         }
-        for k in ("slab", "generation_s", "step_ms_min_max"):
+        for k in ("slab", "generation_s", "step_ms_min_max", "result_sha256"):
             if k in head:
                 line["config" if k == "slab" else k] = ({**line["config"], "slab_rank0": head[k]} if k == "slab"
                                                          else head[k])
@@ -1205,6 +1278,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 8e6-needle and 2e5-cylinder figures")
     ap.add_argument("--batch-rois", type=int, default=256, help="ROIs of the batched measurement (0 skips it)")
     ap.add_argument("--batch-cell-scale", type=float, default=1.0)
+    ap.add_argument("--soft-cell-scale", type=float, default=0.5, help="cell edge / r_cut of the smoothed-RDF grids")
     ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
     ap.add_argument("--split", action="store_true", help="the query in passes (with --no-autotune; ps_grid_opts.split)")

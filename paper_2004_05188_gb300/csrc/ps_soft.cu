@@ -16,9 +16,18 @@
 // and odd about c_m, i.e. a relative error ~1e-7 that averages out.
 // Adjoint: W, W', W'' are tabulated on the same fine grid (FP64, stored as
 // float) and evaluated per pair by the same second-order expansion.  Pairs are
-// recomputed, never stored.  Pass A (one lane per central i) writes dL/dx_i and
-// accumulates dL/ds; pass B (one lane per neighbour j, candidates = centrals)
-// adds dL/dx_j.  Each gradient has one owner: no atomics on the gradient.
+// recomputed, never stored.  Record k's gradient gathers every pair it is in,
+// W s (x_k - x_m)/d, once for each role: as the central (m a neighbour) and as
+// the neighbour (m a central).  When the centrals are neighbour records, one
+// pass has every neighbour record own its gradient, with the pair weighted by
+// the central flags of both ends (0, 1 or 2); otherwise pass A (one lane per
+// central) writes and pass B (one lane per neighbour, candidates = centrals)
+// adds.  Each gradient has one owner: no atomics on the gradient.  dL/ds sums
+// W d over the pairs with a central owner.
+// Both kernels test the candidates two at a time with packed float32; the
+// forward compacts the in-range pairs of every 16 candidates into a warp list
+// that all lanes bin; the adjoint runs the pair code under a branch per
+// candidate (its per-pair work needs the owner's accumulators).
 #include <cmath>
 #include <cstring>
 
@@ -50,6 +59,7 @@ struct SoftArgs {
   double* M2;
   // adjoint
   const float* T;          // [3][n_fine]: W, W', W'' at the fine-bin centres
+  const uint32_t* pfx;     // one-pass adjoint: central prefix over the neighbour records
   float* grad;             // [n][3]
   double* grad_s;
   int pass_b;              // 0: owners are centrals (write), 1: owners are neighbours (add, sign flipped)
@@ -71,15 +81,174 @@ __device__ __forceinline__ void soft_run(const SoftArgs& a, const Geo& ng, uint3
   }
 }
 
-// Iterates the items of the owner list; for every owner lane and in-range
-// candidate calls f(lane_has_owner, p (owner record), q (candidate), d2).
-struct NoHook {
-  __device__ void operator()(uint32_t, uint32_t) const {}
-};
+// Half stencil of cell c for the forward over unordered pairs, run r of (2s+1)s + s + 1: the
+// rows above (dz > 0, every dy), the rows ahead in the same plane (dz = 0, dy > 0), both over
+// cx-s .. cx+s, and the cells after c in its own row (cx+1 .. cx+s).  With the pairs inside the
+// cell (j > i) every unordered pair within the stencil is met once.
+__device__ __forceinline__ void soft_half_run(const SoftArgs& a, const Geo& ng, uint32_t c, uint32_t r,
+                                              uint32_t& src, uint32_t& len) {
+  const int s = a.stencil, wd = 2 * s + 1;
+  const uint32_t cx = c % ng.dims[0], cy = (c / ng.dims[0]) % ng.dims[1], cz = c / (ng.dims[0] * ng.dims[1]);
+  src = 0;
+  len = 0;
+  int dy, dz;
+  uint32_t xlo = cx >= (uint32_t)s ? cx - s : 0;
+  const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
+  if ((int)r < s * wd) {
+    dz = 1 + (int)r / wd, dy = (int)r % wd - s;
+  } else if ((int)r < s * wd + s) {
+    dz = 0, dy = 1 + (int)r - s * wd;
+  } else if ((int)r == s * wd + s) {
+    dz = 0, dy = 0, xlo = cx + 1;
+  } else {
+    return;
+  }
+  const int y = (int)cy + dy, z = (int)cz + dz;
+  if (y < 0 || y >= (int)ng.dims[1] || z >= (int)ng.dims[2] || xlo > xhi) return;
+  const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+  src = a.nstart[row + xlo];
+  len = a.nstart[row + xhi + 1] - src;
+}
 
-template <class F, class B, class E, class H = NoHook>
-__device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint32_t* rsrc, uint32_t* rpre, F&& f,
-                                           B&& begin_owner, E&& end_owner, H&& item_hook = H()) {
+// Iterates the items of the owner list with the candidates staged 32 at a time as interleaved
+// pairs (xa xb ya yb za zb wa wb) and tested two at a time with packed float32 math; the
+// in-range pairs of every half-batch of 16 candidates go to a warp list that all lanes then
+// process: hit(d2, weight) for each.  item_hook(cnt, n_cand) runs once per item.
+// SYM (centrals among the neighbour records): owners are the neighbour records, each pair is met
+// once (the half stencil and the later records of the owner's cell) and weighs c_i + c_j, the
+// central flags of its ends from the central prefix; the staged .w is rc^2 for a central
+// candidate and -1 otherwise, the range max(owner's, candidate's), and the sign bit of a listed
+// d2 marks weight 2.  Otherwise owners are the centrals, candidates their full stencil of
+// neighbours, .w the ion index (the owner itself is skipped), weight 1.
+template <bool SYM, class H, class I>
+__device__ __forceinline__ void soft_items_listed(const SoftArgs& a, float* bf, uint32_t* rsrc, uint32_t* rpre,
+                                                  float* wlist, H&& hit, I&& item_hook) {
+  const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+  const Geo ng = *a.ngeo;
+  const uint32_t n_front = a.ogeo->work_n2, n_items = n_front + a.ogeo->work_n3;
+  const int s = a.stencil, wd = 2 * s + 1;
+  const int n_runs = SYM ? s * wd + s + 1 : wd * wd;
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(&a.ogeo->work_next2, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const uint2 it = work_item(a.oitem, a.ocap, n_front, item);
+    const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
+    const uint32_t c0 = a.ostart[c] + first;
+    uint32_t src = 0, len = 0;
+    if (SYM)
+      soft_half_run(a, ng, c, lane, src, len);
+    else
+      soft_run(a, ng, c, lane, src, len);
+    uint32_t pre = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= (uint32_t)o) pre += y;
+    }
+    const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
+    __syncwarp();
+    if (lane < (uint32_t)n_runs) {
+      rsrc[lane] = src;
+      rpre[lane + 1] = pre;
+    }
+    if (lane == 0) rpre[0] = 0;
+    __syncwarp();
+    const uint32_t a1 = SYM ? a.ostart[c + 1] : 0u;  // end of the owner's cell
+    item_hook(cnt, n_cand + (SYM ? a1 - c0 : 0u));
+    const bool valid = lane < cnt;
+    float4 p = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    float elane = -INFINITY;
+    uint32_t pidx = ~0u, w2lane = 0u;
+    if (valid) {
+      p = a.orec[c0 + lane];
+      if (SYM) {
+        const bool cen = __ldg(a.pfx + c0 + lane + 1) > __ldg(a.pfx + c0 + lane);
+        elane = cen ? a.rc2u : -1.f;
+        w2lane = cen ? 0x80000000u : 0u;
+      } else {
+        pidx = __float_as_uint(p.w);
+        elane = a.rc2u;
+      }
+    }
+    if (SYM && valid) {
+      // pairs inside the owner's cell, j > i, each lane on its own (a small share of the pairs)
+      const float ci = w2lane ? 1.f : 0.f;
+      for (uint32_t j = c0 + lane + 1; j < a1; ++j) {
+        const float4 q = __ldg(a.nrec + j);
+        const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+        const float wt = ci + (float)(__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+        if (d2 < a.rc2u && wt > 0.f) hit(d2, wt);
+      }
+    }
+    const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
+    int rr = 0;
+    auto fetch = [&](uint32_t pos) -> float4 {
+      if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, SYM ? -1.f : __uint_as_float(~0u));
+      while (pos >= rpre[rr + 1]) ++rr;
+      const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
+      float4 q = __ldg(a.nrec + j);
+      if (SYM) q.w = __ldg(a.pfx + j + 1) > __ldg(a.pfx + j) ? a.rc2u : -1.f;
+      return q;
+    };
+    float4 nxt = fetch(lane);
+    for (uint32_t b = 0; b < n_cand; b += 32) {
+      __syncwarp();
+      {
+        float* d = bf + (lane >> 1) * 8 + (lane & 1);
+        d[0] = nxt.x, d[2] = nxt.y, d[4] = nxt.z, d[6] = nxt.w;
+      }
+      __syncwarp();
+      nxt = fetch(b + 32 + lane);
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        uint32_t nh = 0;
+#pragma unroll 2
+        for (uint32_t u = 0; u < 8; ++u) {
+          const uint32_t t = 8 * half + u;
+          const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
+          const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
+          float d2a, d2b, wa, wb;
+          dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
+          f2_unpack(zw.y, wa, wb);
+          bool ha, hb;
+          uint32_t va, vb;
+          if (SYM) {
+            ha = d2a < fmaxf(elane, wa), hb = d2b < fmaxf(elane, wb);
+            va = __float_as_uint(d2a) | (~__float_as_uint(wa) & w2lane);
+            vb = __float_as_uint(d2b) | (~__float_as_uint(wb) & w2lane);
+          } else {
+            ha = d2a < elane && __float_as_uint(wa) != pidx, hb = d2b < elane && __float_as_uint(wb) != pidx;
+            va = __float_as_uint(d2a), vb = __float_as_uint(d2b);
+          }
+          const uint32_t ba = __ballot_sync(0xffffffffu, ha);
+          reinterpret_cast<uint32_t*>(wlist)[ha ? nh + __popc(ba & lt) : 512 + lane] = va;
+          nh += __popc(ba);
+          const uint32_t bb = __ballot_sync(0xffffffffu, hb);
+          reinterpret_cast<uint32_t*>(wlist)[hb ? nh + __popc(bb & lt) : 512 + lane] = vb;
+          nh += __popc(bb);
+        }
+        __syncwarp();
+        for (uint32_t h = lane; h < nh; h += 32) {
+          const uint32_t v = reinterpret_cast<const uint32_t*>(wlist)[h];
+          hit(__uint_as_float(v & 0x7FFFFFFFu), (v >> 31) ? 2.f : 1.f);
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// Same iteration for the adjoint, where every in-range pair updates its owner lane's
+// accumulators: f(p, qx, qy, qz, qw, d2) under a branch per candidate (queueing the pairs
+// first measured slower).  ONE: owners and candidates are the neighbour records and the staged
+// .w is the candidate's central flag (from the central prefix); a pair counts when d2 > 0 and
+// either end is central.  Otherwise .w is the ion index and the owner itself is skipped.
+// begin_owner(valid, p, c_own) / end_owner(valid, p) bracket each owner.
+template <bool ONE, class F, class B, class E>
+__device__ __forceinline__ void soft_items_owned(const SoftArgs& a, float* bf, uint32_t* rsrc, uint32_t* rpre,
+                                                 F&& f, B&& begin_owner, E&& end_owner) {
   const uint32_t lane = threadIdx.x & 31;
   const Geo ng = *a.ngeo;
   const uint32_t n_front = a.ogeo->work_n2, n_items = n_front + a.ogeo->work_n3;
@@ -108,29 +277,53 @@ __device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint3
     }
     if (lane == 0) rpre[0] = 0;
     __syncwarp();
-    item_hook(cnt, n_cand);
     const bool valid = lane < cnt;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) p = a.orec[c0 + lane];
-    begin_owner(valid, p);
+    float c_own = 0.f;
+    if (valid) {
+      p = a.orec[c0 + lane];
+      if (ONE) c_own = (float)(__ldg(a.pfx + c0 + lane + 1) - __ldg(a.pfx + c0 + lane));
+    }
+    const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
+    const float emax = valid ? a.rc2u : -INFINITY;
+    const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
+    begin_owner(valid, p, c_own);
     int rr = 0;
     auto fetch = [&](uint32_t pos) -> float4 {
-      if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(~0u));
+      if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, ONE ? 0.f : __uint_as_float(~0u));
       while (pos >= rpre[rr + 1]) ++rr;
-      return __ldg(a.nrec + rsrc[rr] + (pos - rpre[rr]));
+      const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
+      float4 q = __ldg(a.nrec + j);
+      if (ONE) q.w = (float)(__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+      return q;
+    };
+    auto hit = [&](float d2, float w) -> bool {
+      if (ONE) return d2 < emax && d2 > 0.f && c_own + w > 0.f;
+      return d2 < emax && __float_as_uint(w) != pidx;
     };
     float4 nxt = fetch(lane);
     for (uint32_t b = 0; b < n_cand; b += 32) {
       __syncwarp();
-      buf[lane] = nxt;
+      {
+        float* d = bf + (lane >> 1) * 8 + (lane & 1);
+        d[0] = nxt.x, d[2] = nxt.y, d[4] = nxt.z, d[6] = nxt.w;
+      }
       __syncwarp();
       nxt = fetch(b + 32 + lane);
-      if (valid) {
-#pragma unroll 4
-        for (int t = 0; t < 32; ++t) {
-          const float4 q = buf[t];
-          const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-          if (d2 < a.rc2u && __float_as_uint(q.w) != __float_as_uint(p.w)) f(p, q, d2);
+#pragma unroll 2
+      for (uint32_t t = 0; t < 16; ++t) {
+        const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
+        const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
+        float d2a, d2b, xa, xb, ya, yb, za, zb, wa, wb;
+        dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
+        f2_unpack(zw.y, wa, wb);
+        if (hit(d2a, wa)) {
+          f2_unpack(xy.x, xa, xb), f2_unpack(xy.y, ya, yb), f2_unpack(zw.x, za, zb);
+          f(p, xa, ya, za, wa, d2a);
+        }
+        if (hit(d2b, wb)) {
+          f2_unpack(xy.x, xa, xb), f2_unpack(xy.y, ya, yb), f2_unpack(zw.x, za, zb);
+          f(p, xb, yb, zb, wb, d2b);
         }
       }
     }
@@ -141,13 +334,16 @@ __device__ __forceinline__ void soft_items(const SoftArgs& a, float4* buf, uint3
 // ---------------------------------------------------------------------------
 // forward: fine-grid moments
 // ---------------------------------------------------------------------------
+template <bool SYM>
 __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
   griddep_wait();
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float4 s_buf[8][32];
+  __shared__ float s_hits[8][512 + 32];  // per warp: one half-batch's in-range d2 + a trash row
   __shared__ uint32_t s_rsrc[8][kSoftRuns], s_rpre[8][kSoftRuns + 1];
-  // 32-bit counts per CTA; a warp whose item could push the CTA past 2^31 pairs writes to global instead
+  // 32-bit counts per CTA; a warp whose item could push the CTA past 2^31 (weighted) pairs writes
+  // to global instead
   uint32_t* sM0 = reinterpret_cast<uint32_t*>(smem);
   float* sM1 = reinterpret_cast<float*>(smem + a.n_fine * 4);
   float* sM2 = reinterpret_cast<float*>(smem + a.n_fine * 8);
@@ -159,31 +355,32 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
   const uint32_t w = threadIdx.x >> 5;
   const float s = a.scale, inv_w = a.inv_w, wf = a.w, rc = a.rc;
   const uint32_t nf = a.n_fine;
-  auto pair = [&](const float4& p, const float4& q, float d2) {
+  // one pair at distance sqrt(d2) with weight wt (1 or 2) into the fine-grid moments
+  auto pair = [&](float d2, float wt) {
     const float u = s * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
     if (!(u < rc)) return;
     uint32_t m = (uint32_t)(u * inv_w);
     m = m < nf ? m : nf - 1;
     const float delta = u - ((float)m + 0.5f) * wf;
+    const float wd = wt * delta;
     if (glob) {
-      atomicAdd(&a.M0[m], 1ull);
-      atomicAdd(&a.M1[m], (double)delta);
-      atomicAdd(&a.M2[m], (double)delta * (double)delta);
+      atomicAdd(&a.M0[m], (unsigned long long)wt);
+      atomicAdd(&a.M1[m], (double)wd);
+      atomicAdd(&a.M2[m], (double)wd * (double)delta);
     } else {
-      atomicAdd(&sM0[m], 1u);
-      atomicAdd(&sM1[m], delta);
-      atomicAdd(&sM2[m], delta * delta);
+      atomicAdd(&sM0[m], (uint32_t)wt);
+      atomicAdd(&sM1[m], wd);
+      atomicAdd(&sM2[m], wd * delta);
     }
   };
   auto bound = [&](uint32_t cnt, uint32_t n_cand) {
     unsigned long long old = 0;
-    const unsigned long long inc = (unsigned long long)cnt * n_cand;
+    const unsigned long long inc = (unsigned long long)cnt * n_cand * (SYM ? 2u : 1u);
     if ((threadIdx.x & 31) == 0) old = atomicAdd(&s_pairs, inc);
     old = __shfl_sync(0xffffffffu, old, 0);
     glob = old + inc >= (1ull << 31);
   };
-  auto nop = [](bool, const float4&) {};
-  soft_items(a, s_buf[w], s_rsrc[w], s_rpre[w], pair, nop, nop, bound);
+  soft_items_listed<SYM>(a, reinterpret_cast<float*>(s_buf[w]), s_rsrc[w], s_rpre[w], s_hits[w], pair, bound);
   __syncthreads();
   for (uint32_t m = threadIdx.x; m < nf; m += blockDim.x) {
     if (sM0[m]) {
@@ -263,6 +460,11 @@ __global__ void __launch_bounds__(256) k_soft_table(const float* __restrict__ G,
 // ---------------------------------------------------------------------------
 // adjoint passes
 // ---------------------------------------------------------------------------
+// ONE: a single pass over the neighbour records when the centrals are among them; every record
+// owns its gradient, W s (x_o - x_c)/d times the pair's weight (central flags of both ends
+// added), and the central owners accumulate dL/ds.  Otherwise pass A (owners = centrals, write)
+// and pass B (owners = neighbours, add).
+template <bool ONE>
 __global__ void __launch_bounds__(256) k_soft_bwd(const SoftArgs a) {
   griddep_wait();
   griddep_launch();
@@ -276,11 +478,11 @@ __global__ void __launch_bounds__(256) k_soft_bwd(const SoftArgs a) {
   const uint32_t w = threadIdx.x >> 5;
   const float s = a.scale, inv_w = a.inv_w, wf = a.w, rc = a.rc;
   const uint32_t nf = a.n_fine;
-  float gx = 0.f, gy = 0.f, gz = 0.f;
+  float gx = 0.f, gy = 0.f, gz = 0.f, c_self = 0.f;
   double gs_lane = 0.0;
   float gs_item = 0.f;
-  auto begin = [&](bool, const float4&) { gx = gy = gz = 0.f, gs_item = 0.f; };
-  auto pair = [&](const float4& p, const float4& q, float d2) {
+  auto begin = [&](bool, const float4&, float c_own) { gx = gy = gz = 0.f, gs_item = 0.f, c_self = c_own; };
+  auto pair = [&](const float4& p, float qx, float qy, float qz, float qw, float d2) {
     const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
     const float d = d2 * rs;
     const float u = s * d;
@@ -289,17 +491,17 @@ __global__ void __launch_bounds__(256) k_soft_bwd(const SoftArgs a) {
     m = m < nf ? m : nf - 1;
     const float delta = u - ((float)m + 0.5f) * wf;
     const float W = sT[m] + delta * (sT[nf + m] + 0.5f * delta * sT[2 * nf + m]);
-    const float f = W * s * rs;  // W s / d (0 for coincident ions)
-    gx += f * (p.x - q.x);
-    gy += f * (p.y - q.y);
-    gz += f * (p.z - q.z);
-    gs_item += W * d;
+    const float f = W * s * rs * (ONE ? c_self + qw : 1.f);  // W s / d (0 for coincident ions), weighted
+    gx += f * (p.x - qx);
+    gy += f * (p.y - qy);
+    gz += f * (p.z - qz);
+    if (!ONE || c_self > 0.f) gs_item += W * d;
   };
   auto end = [&](bool valid, const float4& p) {
     if (!valid) return;
     const uint32_t idx = __float_as_uint(p.w);
     float* g = a.grad + 3 * (int64_t)idx;
-    if (a.pass_b) {
+    if (!ONE && a.pass_b) {
       // owners are neighbours j: dL/dx_j = -sum W s (x_i - x_j)/d, here p = x_j, q = x_i
       g[0] += gx, g[1] += gy, g[2] += gz;
     } else {
@@ -307,8 +509,8 @@ __global__ void __launch_bounds__(256) k_soft_bwd(const SoftArgs a) {
       gs_lane += (double)gs_item;
     }
   };
-  soft_items(a, s_buf[w], s_rsrc[w], s_rpre[w], pair, begin, end);
-  if (!a.pass_b) {
+  soft_items_owned<ONE>(a, reinterpret_cast<float*>(s_buf[w]), s_rsrc[w], s_rpre[w], pair, begin, end);
+  if (ONE || !a.pass_b) {
     for (int o = 16; o > 0; o >>= 1) gs_lane += __shfl_xor_sync(0xffffffffu, gs_lane, o);
     if ((threadIdx.x & 31) == 0) s_gs[w] = gs_lane;
     __syncthreads();
@@ -403,6 +605,26 @@ static int launch_grid_for(const ps_grid* g, const void* kern, uint32_t smem, in
   return PS_OK;
 }
 
+// The centrals are neighbour records (the central list then carries the central prefix over the
+// neighbour records, g->cr).
+static bool centrals_in_neighbours(const ps_grid* g, const uint64_t ctr_mask[4]) {
+  bool subset = !g->pack_type;
+  for (int w = 0; w < 4; ++w) subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
+  return subset;
+}
+
+// Owners = the neighbour records: warp items over the non-empty neighbour cells.
+static int nbr_items(ps_grid* g, SoftArgs& sa, cudaStream_t s, uint32_t kid) {
+  PS_LAUNCH(kid, s, PS_CUDA(launch_pdl(k_reset_items, 1, 32, 0, s, g->nbr.geo)));
+  PS_LAUNCH(kid, s, PS_CUDA(launch_pdl(k_make_items, g->num_sms * 4, 256, 0, s, g->nbr.count, g->nbr.geo, g->nbr_witem)));
+  sa.orec = g->nbr.rec;
+  sa.ostart = g->nbr.start;
+  sa.oitem = g->nbr_witem;
+  sa.ocap = g->item_cap;
+  sa.ogeo = g->nbr.geo;
+  return PS_OK;
+}
+
 int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                  ps_bins bins, float* d_h, cudaStream_t s) {
   SoftArgs sa;
@@ -417,11 +639,6 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   z.n[0] = z.n[1] = z.n[2] = sa.n_fine;
   rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z);
   if (rc) return rc;
-  sa.orec = g->ctr.rec;
-  sa.ostart = g->ctr.start;
-  sa.oitem = g->ctr.witem;
-  sa.ocap = g->item_cap;
-  sa.ogeo = g->ctr.geo;
   sa.nrec = g->nbr.rec;
   sa.nstart = g->nbr.start;
   sa.ngeo = g->nbr.geo;
@@ -430,9 +647,24 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
   sa.M2 = g->soft_m2;
   const uint32_t smem = sa.n_fine * 12;
   int blocks = 0;
-  rc = launch_grid_for(g, (const void*)k_soft_fwd, smem, &blocks);
-  if (rc) return rc;
-  PS_LAUNCH(PS_KID_SOFT_FWD, s, PS_CUDA(launch_pdl(k_soft_fwd, blocks, 256, smem, s, sa)));
+  if (centrals_in_neighbours(g, ctr_mask)) {
+    // unordered pairs of neighbour records, weighted by the central flags of both ends
+    rc = launch_grid_for(g, (const void*)k_soft_fwd<true>, smem, &blocks);
+    if (rc) return rc;
+    rc = nbr_items(g, sa, s, PS_KID_SOFT_FWD);
+    if (rc) return rc;
+    sa.pfx = reinterpret_cast<const uint32_t*>(g->cr);
+    PS_LAUNCH(PS_KID_SOFT_FWD, s, PS_CUDA(launch_pdl(k_soft_fwd<true>, blocks, 256, smem, s, sa)));
+  } else {
+    rc = launch_grid_for(g, (const void*)k_soft_fwd<false>, smem, &blocks);
+    if (rc) return rc;
+    sa.orec = g->ctr.rec;
+    sa.ostart = g->ctr.start;
+    sa.oitem = g->ctr.witem;
+    sa.ocap = g->item_cap;
+    sa.ogeo = g->ctr.geo;
+    PS_LAUNCH(PS_KID_SOFT_FWD, s, PS_CUDA(launch_pdl(k_soft_fwd<false>, blocks, 256, smem, s, sa)));
+  }
   PS_LAUNCH(PS_KID_SOFT_FWD, s,
             PS_CUDA(launch_pdl(k_soft_finalize, bins.n_bins, 256, 0, s, g->soft_m0, g->soft_m1, g->soft_m2, sa.n_fine, w, bins.r0,
                                                         bins.dr, (double)sigma, d_h)));
@@ -459,32 +691,41 @@ int soft_backward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], flo
   sa.grad_s = g->soft_gs;
   const uint32_t smem = sa.n_fine * 12;
   int blocks = 0;
-  rc = launch_grid_for(g, (const void*)k_soft_bwd, smem, &blocks);
-  if (rc) return rc;
-  // pass A: owners = centrals, candidates = neighbours
-  sa.orec = g->ctr.rec;
-  sa.ostart = g->ctr.start;
-  sa.oitem = g->ctr.witem;
-  sa.ocap = g->item_cap;
-  sa.ogeo = g->ctr.geo;
-  sa.nrec = g->nbr.rec;
-  sa.nstart = g->nbr.start;
-  sa.ngeo = g->nbr.geo;
-  sa.pass_b = 0;
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd, blocks, 256, smem, s, sa)));
-  // pass B: owners = neighbours, candidates = centrals
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_reset_items, 1, 32, 0, s, g->nbr.geo)));
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_make_items, g->num_sms * 4, 256, 0, s, g->nbr.count, g->nbr.geo, g->nbr_witem)));
-  sa.orec = g->nbr.rec;
-  sa.ostart = g->nbr.start;
-  sa.oitem = g->nbr_witem;
-  sa.ocap = g->item_cap;
-  sa.ogeo = g->nbr.geo;
-  sa.nrec = g->ctr.rec;
-  sa.nstart = g->ctr.start;
-  sa.ngeo = g->nbr.geo;
-  sa.pass_b = 1;
-  PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd, blocks, 256, smem, s, sa)));
+  if (centrals_in_neighbours(g, ctr_mask)) {
+    // one pass: the central prefix over the neighbour records (built with the central list) gives
+    // every record's central flag
+    rc = launch_grid_for(g, (const void*)k_soft_bwd<true>, smem, &blocks);
+    if (rc) return rc;
+    rc = nbr_items(g, sa, s, PS_KID_SOFT_BWD);
+    if (rc) return rc;
+    sa.nrec = g->nbr.rec;
+    sa.nstart = g->nbr.start;
+    sa.ngeo = g->nbr.geo;
+    sa.pfx = reinterpret_cast<const uint32_t*>(g->cr);
+    PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd<true>, blocks, 256, smem, s, sa)));
+  } else {
+    rc = launch_grid_for(g, (const void*)k_soft_bwd<false>, smem, &blocks);
+    if (rc) return rc;
+    // pass A: owners = centrals, candidates = neighbours
+    sa.orec = g->ctr.rec;
+    sa.ostart = g->ctr.start;
+    sa.oitem = g->ctr.witem;
+    sa.ocap = g->item_cap;
+    sa.ogeo = g->ctr.geo;
+    sa.nrec = g->nbr.rec;
+    sa.nstart = g->nbr.start;
+    sa.ngeo = g->nbr.geo;
+    sa.pass_b = 0;
+    PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd<false>, blocks, 256, smem, s, sa)));
+    // pass B: owners = neighbours, candidates = centrals
+    rc = nbr_items(g, sa, s, PS_KID_SOFT_BWD);
+    if (rc) return rc;
+    sa.nrec = g->ctr.rec;
+    sa.nstart = g->ctr.start;
+    sa.ngeo = g->nbr.geo;
+    sa.pass_b = 1;
+    PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_bwd<false>, blocks, 256, smem, s, sa)));
+  }
   PS_LAUNCH(PS_KID_SOFT_BWD, s, PS_CUDA(launch_pdl(k_soft_gs_out, 1, 32, 0, s, g->soft_gs, d_grad_s)));
   PS_CUDA(cudaGetLastError());
   return PS_OK;

@@ -104,8 +104,13 @@ def combine(dist, out: dict, device=None) -> None:
     status = meta[3:4].clone()
     flat = torch.cat(parts + [meta.reshape(-1)])
     flat[-meta.numel() + 3] = 0
+    host = dist.get_backend() == "gloo" and flat.is_cuda  # gloo sums host tensors
+    if host:
+        flat, status = flat.cpu(), status.cpu()
     dist.all_reduce(flat)
     dist.all_reduce(status, op=dist.ReduceOp.MAX)
+    if host:
+        flat, status = flat.to(meta.device), status.to(meta.device)
     o = 0
     for k in SUM_KEYS:
         if out.get(k) is not None:

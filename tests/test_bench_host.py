@@ -33,12 +33,40 @@ def test_candidate_tests_brute_force(stencil, h):
 
 
 def test_stored_traffic_guard():
-    cfg = {"all-all": {"cell_scale": 0.5, "dense_min": 0, "split": 1}, "Sc-Sc": {"cell_scale": 0.5, "dense_min": 0, "split": 1}}
+    cfg = {"all-all": {"cell_scale": 0.5, "dense_min": 0, "split": 1}, "Sc-Sc": {"cell_scale": 0.5, "dense_min": 0, "split": 0}}
     v = bench.stored_traffic("needle2g", cfg)
-    # either the stored figure (sources unchanged since the capture) or None; never for another setup
-    assert v is None or v > 0
+    # either the stored figures (sources unchanged since the capture) or None; never for another setup
+    assert v is None or (v["combination"] == "all-all" and v["kernels"]["rdf_sym"] > 0)
     assert bench.stored_traffic("needle2g", {**cfg, "Sc-Sc": {"cell_scale": 1.0, "dense_min": 0, "split": 0}}) is None
     assert bench.stored_traffic("cylinder200k", cfg) is None
+
+
+def _combo(name, split, near, sym, n_pairs):
+    by = {"query": near, "rdf_sym": sym} if split else {"query": near}
+    return dict(name=name, n_nbr=1000, n_cells=100, n_central=900, n_ctr_typed=950, n_pairs_local=n_pairs,
+                subset=True, candidates=near + sym, candidates_by_pass=by, split=split)
+
+
+def test_rooflines_dominant_kernel_and_traffic():
+    """The roofline names the query family with the most time; its traffic is reported per launch
+    only when every launch of that family belongs to the recorded combination."""
+    peaks = {"fp32_scalar_gops": 40000.0, "fp32_packed_gops": 40000.0, "smem_atomic_gops": 10000.0,
+             "num_sms": 152, "sm_mhz": 2070.0}
+    st = {"n_ions": 1000, "combos": [_combo("all-all", True, 4e9, 1e10, 5e8), _combo("Sc-Sc", False, 1e8, 0, 1e6)]}
+    zero = (0, 0.0)
+    prof = {f: zero for f in bench.FAMS}
+    prof.update(query=(4, 100.0), knn_full=(2, 4.0), rdf_sym=(2, 300.0), scan=(4, 10.0))
+    traffic = {"combination": "all-all", "kernels": {"query": 5e9, "knn_full": 1e8, "rdf_sym": 2e10}}
+    r = bench.rooflines(prof, st, 2, peaks, 6000.0, "measured", traffic)
+    assert r["family"] == "rdf_sym" and r["traffic"] == 2e10
+    sym_tf = 9 * 1e10 * 2 / 0.3 / 1e12
+    assert abs(r["achieved"] - sym_tf) < 1e-9 and abs(r["frac"] - sym_tf / 40.0) < 1e-9
+    # k_query_warp also runs for Sc-Sc: no per-launch traffic for that family, the record kept beside it
+    assert r["by_kernel"]["query"]["traffic"] is None and r["by_kernel"]["query"]["traffic_recorded"] == 5e9
+    assert r["by_kernel"]["knn_full"]["achieved_tflops"] is None
+    allq = 9 * (4e9 + 1e10 + 1e8) * 2 / 0.404 / 1e12
+    assert abs(r["all_query_passes"]["achieved"] - allq) < 1e-6
+    assert bench.rooflines(prof, st, 2, peaks, 6000.0, "measured", None)["traffic"] is None
 
 
 @pytest.mark.parametrize("shares", [1, 3, 7])

@@ -11,7 +11,10 @@
   that slab plus an r_cut halo of neighbours (split into x-strips over the host cores, which
   add up exactly): the RDF, kNN, not-found and pair counts bin for bin, and the full-size
   run's per-central k-th distance and in-range count of every slab central;
-* Sc-Sc, k = 10, same bins and d_srf: the complete oracle, every bin.
+* Sc-Sc, k = 10, same bins and d_srf: the complete oracle, every bin;
+* the launch configuration the benchmark times (half-size cells, the query in passes): the
+  whole-cloud all-all histograms equal to the 27-cell run's bin for bin, the three slabs against
+  the same oracle results, and Sc-Sc against the complete oracle, with and without the passes.
 
 Needs ~40 GB of host memory and ~190 GB of device memory; takes a few minutes.
 """
@@ -99,7 +102,8 @@ def test_needle_2e9_full_size(ps, orc, spec):
     central = d >= np.float32(2.0)
     assert n_c == int(central.sum())
     rdf = out["rdf"].cpu().numpy()
-    knn = out["knn"].cpu().numpy()[0]
+    knn_all = out["knn"].cpu().numpy()
+    knn = knn_all[0]
     nw = out["n_within"]
     kth = out["kth_d2"][0]
     Cm = torch.from_numpy(central).cuda()
@@ -137,6 +141,7 @@ def test_needle_2e9_full_size(ps, orc, spec):
     slabs = {"tip": (nk - 40, nk - 8), "mid": (nk // 2, nk // 2 + 2), "base": (10, 11)}
     halo = 16  # layers: 6.5 nm > r_cut + the z jitter on both sides
     Dm = torch.empty_like(D)
+    refs = {}
     for name, (k0, k1) in slabs.items():
         lo, hi = int(off[k0]), int(off[k1])
         a, z = int(off[max(0, k0 - halo)]), xyz[:, 2]
@@ -149,6 +154,7 @@ def test_needle_2e9_full_size(ps, orc, spec):
         Dm[lo:hi] = D[lo:hi]
         o = ps.spatstat(g, Dm, "all", 2.0, bins, [10])
         ref, idx, kref, nref = _oracle_slab(orc, xyz[a:e], t[a:e], d[a:e], lo - a, hi - a, 2.0, bins, [10], threads)
+        refs[name] = (lo, hi, ref)
         m = o["meta"].cpu().numpy()
         assert m[3] == 0 and ref["n_central"] > 1e5, (name, ref["n_central"])
         assert m[0] == ref["n_central"] and m[1] == ref["n_pairs"] and m[4] == ref["not_found"][0], name
@@ -158,16 +164,37 @@ def test_needle_2e9_full_size(ps, orc, spec):
         np.testing.assert_array_equal(nw_h[idx + a], nref)
         np.testing.assert_array_equal(kth_h[idx + a], kref)
         print(f"\n  {name} slab: {ref['n_central']} centrals, {ref['n_pairs']} pairs, every bin equal")
-    del Dm
 
     # ---- Sc-Sc, k = 10: the complete oracle ----
     g.build(X, T, [1], 2.0)
     o = ps.spatstat(g, D, [1], 2.0, bins, [10])
     r = orc.spatstat(xyz, t, d, [1], [1], 2.0, *bins, [10])
-    np.testing.assert_array_equal(o["rdf"].cpu().numpy().astype(np.uint64), r["rdf"])
-    np.testing.assert_array_equal(o["knn"].cpu().numpy().astype(np.uint64), r["knn"])
-    m = o["meta"].cpu().numpy()
-    assert m[0] == r["n_central"] and m[1] == r["n_pairs"] and m[4] == r["not_found"][0]
+
+    def same_as_oracle(o, r, what):
+        np.testing.assert_array_equal(o["rdf"].cpu().numpy().astype(np.uint64), r["rdf"], err_msg=what)
+        np.testing.assert_array_equal(o["knn"].cpu().numpy().astype(np.uint64), r["knn"], err_msg=what)
+        m = o["meta"].cpu().numpy()
+        assert m[3] == 0 and m[0] == r["n_central"] and m[1] == r["n_pairs"] and m[4] == r["not_found"][0], what
+
+    same_as_oracle(o, r, "Sc-Sc")
+    g.close()
+
+    # ---- the benchmark's launch configuration: half-size cells, the query in passes ----
+    g = ps.Grid(n, 0.5, 0, True)
+    g.build(X, T, "all", 2.0)
+    o = ps.spatstat(g, D, "all", 2.0, bins, [10])
+    np.testing.assert_array_equal(o["rdf"].cpu().numpy(), rdf)
+    np.testing.assert_array_equal(o["knn"].cpu().numpy(), knn_all)
+    np.testing.assert_array_equal(o["meta"].cpu().numpy(), meta)
+    for name, (lo, hi, ref) in refs.items():
+        Dm.fill_(float("nan"))
+        Dm[lo:hi] = D[lo:hi]
+        same_as_oracle(ps.spatstat(g, Dm, "all", 2.0, bins, [10]), ref, name + " slab, passes")
+    del Dm
+    g.build(X, T, [1], 2.0)
+    for split in (False, True):
+        g.set_query_opts(0, split)
+        same_as_oracle(ps.spatstat(g, D, [1], 2.0, bins, [10]), r, f"Sc-Sc, half-size cells, split={split}")
     g.close()
     print(f"\n2e9 needle: n={n}, generation {gen_s:.1f} s, all-all build+query {gpu_s:.1f} s, "
           f"{n_c} centrals, {int(meta[1])} pairs, Sc-Sc centrals {r['n_central']}")

@@ -74,6 +74,17 @@ def test_soft_type_subsets_and_dsrf(ps, orc, spec):
     assert np.all(gx[lonely] == 0.0)
 
 
+@pytest.mark.parametrize("cell_scale", [1.0, 0.5])
+def test_soft_centrals_within_neighbours(ps, orc, spec, cell_scale):
+    """Centrals a subset of the neighbour set (one adjoint pass, pair weights 0, 1 and 2): type 1
+    ions with d_srf >= 0.6 among neighbours of types {0, 1}; type 2 ions are in no pair."""
+    xyz, t, d = spec.cube(204, 2000, 4.0, (0.5, 0.3, 0.2))
+    G = np.random.default_rng(16).standard_normal(BINS[2])
+    h, gx, gs = _run(ps, xyz, t, d, [0, 1], [1], 0.6, 0.97, G, cell_scale)
+    _check(orc, xyz, t, d, [0, 1], [1], 0.6, 0.97, G, h, gx, gs)
+    assert np.all(gx[t == 2] == 0.0)
+
+
 def test_soft_identities_at_scale(ps, spec):
     """Translation invariance and the scaling identity on a 2e5-ion cylinder (any size)."""
     xyz, t, d = spec.cylinder_small()
