@@ -140,9 +140,35 @@ def stored_traffic(workload: str, kernel_config: dict):
     return None
 
 
-def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26, all_records=False):
+def row_widths(stencil: int, cell_scale: float):
+    """Half-width of each stencil row (dy, dz) of the exact query, [dz + s][dy + s] (-1: none): the
+    cells whose gap to the central cell exceeds r_cut on the cell-edge bound r_cut * cell_scale *
+    (1 + 2^-10) are skipped (the library's rule, restated for the test counts)."""
+    s = int(stencil)
+    f = float(np.float32(cell_scale)) * (1.0 + 1.0 / 1024.0)
+    lim = (1.0 + 1.0 / 1048576.0) ** 2
+
+    def m2(d):
+        m = abs(d) - 1
+        return float(m * m) if m > 0 else 0.0
+
+    out = []
+    for dz in range(-s, s + 1):
+        row = []
+        for dy in range(-s, s + 1):
+            w = -1
+            for dx in range(s + 1):
+                if (m2(dx) + m2(dy) + m2(dz)) * f * f < lim:
+                    w = dx
+            row.append(w)
+        out.append(row)
+    return out
+
+
+def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26, all_records=False, cell_scale=None):
     """Central x candidate tests one query makes on this grid: for every central, the neighbour
-    records in the (2*stencil+1)^3 cells around its cell (clipped at the grid's faces).
+    records in the (2*stencil+1)^3 cells around its cell (clipped at the grid's faces), less the
+    cells the query skips (row_widths; cell_scale None: every cell of the stencil).
     Counted with plain torch ops from the grid geometry (reporting only, untimed), in chunks of
     ions so that the temporaries stay small beside a 2e9-ion cloud.  all_records: every neighbour
     record counts as a central (no type or d_srf filter)."""
@@ -172,10 +198,25 @@ def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26, a
         cnt += torch.bincount(cells(X[a:a + chunk][sel]), minlength=info["n_cells"])
     cnt = cnt.view(dims[2], dims[1], dims[0])
     s = int(stencil)
-    for ax in range(3):  # box sum of width 2s+1 along each axis (exact, int64)
-        c = torch.cumsum(torch.nn.functional.pad(cnt.movedim(ax, -1), (s + 1, s)), dim=-1)
-        cnt = (c[..., 2 * s + 1:] - c[..., : -(2 * s + 1)]).movedim(-1, ax).contiguous()
-        del c
+    widths = row_widths(s, cell_scale) if cell_scale is not None else [[s] * (2 * s + 1)] * (2 * s + 1)
+    if all(w == s for row in widths for w in row):
+        for ax in range(3):  # box sum of width 2s+1 along each axis (exact, int64)
+            c = torch.cumsum(torch.nn.functional.pad(cnt.movedim(ax, -1), (s + 1, s)), dim=-1)
+            cnt = (c[..., 2 * s + 1:] - c[..., : -(2 * s + 1)]).movedim(-1, ax).contiguous()
+            del c
+    else:  # rows of their own widths: x-box sums, shifted over (dy, dz)
+        acc = torch.zeros_like(cnt)
+        Z, Y = dims[2], dims[1]
+        for w in sorted({w for row in widths for w in row if w >= 0}):
+            c = torch.cumsum(torch.nn.functional.pad(cnt, (w + 1, w)), dim=-1)
+            box = torch.nn.functional.pad(c[..., 2 * w + 1:] - c[..., : -(2 * w + 1)], (0, 0, s, s, s, s))
+            del c
+            for dz in range(-s, s + 1):
+                for dy in range(-s, s + 1):
+                    if widths[dz + s][dy + s] == w:
+                        acc += box[s + dz: s + dz + Z, s + dy: s + dy + Y]
+            del box
+        cnt = acc
     cnt = cnt.reshape(-1)
     tot = 0
     for a in range(0, n, chunk):
@@ -779,18 +820,19 @@ def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil, split=Fa
     lut = np.array([bool((int(mc[v >> 6]) >> (v & 63)) & 1) for v in range(256)])
     n_typed = sum(int(np.count_nonzero(lut[t_host[a:a + (1 << 26)]])) for a in range(0, t_host.shape[0], 1 << 26))
     subset = bool(np.all((mc & ~mn) == 0))
-    if split and subset and stencil == 2:
+    cs = g.cell_scale
+    if split and subset and stencil >= 2:
         near = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, 1) if wl["ks"] else 0
-        full = candidate_tests(X, T, D, nbr, nbr, wl["dsrf_min"], info, 2, all_records=True)
+        full = candidate_tests(X, T, D, nbr, nbr, wl["dsrf_min"], info, stencil, all_records=True, cell_scale=cs)
         sym = (full - info["n_nbr"]) // 2
         by_pass = {"query": near, "rdf_sym": sym}
         cands = near + sym
     else:
-        cands = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil)
+        cands = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, stencil, cell_scale=cs)
         by_pass = {"query": cands}
     return dict(name=name, n_nbr=info["n_nbr"], n_cells=info["n_cells"], n_central=int(meta[0]),
                 n_ctr_typed=n_typed, n_pairs_local=int(meta[1]), subset=subset, candidates=cands,
-                candidates_by_pass=by_pass, split=bool(split and subset and stencil == 2))
+                candidates_by_pass=by_pass, split=bool(split and subset and stencil >= 2))
 
 
 def e2e_runner(dev, stream, sets, hosts, step, outs, res_h):
@@ -879,7 +921,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
                  "timings_ms": None}
     else:
         tuned = autotune.tune(X[a:b], T[a:b], D[a:b], nbr0, ctr0, wl["dsrf_min"], bins, wl["ks"],
-                              candidates=((1.0, 0), (0.5, 0), (0.5, 0, 1), (1.0, 128)), reps=2)
+                              candidates=((1.0, 0), (0.5, 0), (0.5, 0, 1), (1 / 3, 0, 1), (1.0, 128)), reps=2)
     cs, dm, sp = tuned["cell_scale"], tuned["dense_min"], int(tuned.get("split", 0))
     # the other combinations keep the cell size (one grid) and tune only the query options
     qopts = {name0: (dm, sp)}
@@ -913,7 +955,7 @@ def measure_sharded(args, wl_name, wl, dev, dist, world, rank, peaks):
 
     # one verified pass per combination (device status, local counts for the rooflines)
     st = {"n_ions": N, "combos": []}
-    stencil = 1 if cs >= 1.0 else 2
+    stencil = grid.stencil
     for (name, ctr, nbr), o in zip(wl["combos"], outs):
         grid.set_query_opts(*qopts[name])
         grid.build(X, T, nbr, r_cut)
@@ -1049,7 +1091,7 @@ def measure_replica(args, wl_name, wl, dev, dist, world, rank, peaks, steps, war
     torch.cuda.synchronize()
     st = {"n_ions": N, "combos": []}
     for (name, ctr, nbr), g, o in zip(wl["combos"], grids, outs):
-        stencil = 1 if tuned[name]["cell_scale"] >= 1.0 else 2
+        stencil = g.stencil
         st["combos"].append(combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t, wl, stencil,
                                         bool(tuned[name].get("split", 0))))
     n_queries = sum(c["n_central"] for c in st["combos"])
@@ -1279,7 +1321,7 @@ def main():
     ap.add_argument("--batch-rois", type=int, default=256, help="ROIs of the batched measurement (0 skips it)")
     ap.add_argument("--batch-cell-scale", type=float, default=1.0)
     ap.add_argument("--soft-cell-scale", type=float, default=0.5, help="cell edge / r_cut of the smoothed-RDF grids")
-    ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 0.5)")
+    ap.add_argument("--cell-scale", type=float, default=1.0, help="cell edge / r_cut (>= 1/3)")
     ap.add_argument("--dense-min", type=int, default=0, help="centrals per cell for the staged CTA kernel (0: never)")
     ap.add_argument("--split", action="store_true", help="the query in passes (with --no-autotune; ps_grid_opts.split)")
     ap.add_argument("--no-autotune", action="store_true",

@@ -96,7 +96,12 @@ typedef struct {
 typedef struct {
   uint32_t struct_size;
   float cell_scale;   /* cell edge = r_cut * cell_scale; 0 = default (1.0).  >= 1: the 27 cells
-                         around a cell are searched; in [0.5, 1): the 125 cells within two cells */
+                         around a cell are searched; in [0.5, 1): the 125 cells within two cells;
+                         in [1/3, 0.5): the 343 cells within three cells.  Cells that cannot hold
+                         a record within r_cut of the cell (their gap to it exceeds r_cut on the
+                         cell-edge lower bound) are skipped by the exact query: the 4 far corner
+                         cells of each octant (32 of 343) for 1/3.  Below 1/3:
+                         PS_ERR_INVALID_ARG */
   uint32_t block;     /* reserved (0) */
   uint32_t dense_min; /* cells with at least this many centrals use the CTA kernel that stages the
                          neighbour cells in shared memory with bulk copies; 0 = never */
@@ -226,7 +231,8 @@ PS_API int ps_rdf_normalise(ps_grid* g, const uint64_t* d_meta, const uint64_t* 
  * ps_sweep: the histogram bins at the largest r_max (n_bins <= 512); rmax_bins
  *   the r_max values as ascending bin counts (last = bins.n_bins); dsrf_min the
  *   ascending d_srf thresholds; type pairs (ctr_mask, nbr_mask), at most two
- *   distinct neighbour sets; k = 1..k_max; cell_scale as in ps_grid_opts.
+ *   distinct neighbour sets; k = 1..k_max; cell_scale as in ps_grid_opts, 0 or >= 0.5
+ *   (PS_ERR_UNSUPPORTED below).
  *   Limit: n_pairs * n_dsrf * n_bins <= 8192.
  * ps_batch_create allocates every grid and accumulator (synchronises).
  * ps_batch_run enqueues the builds of all ROIs, the one persistent query

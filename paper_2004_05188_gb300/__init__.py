@@ -240,7 +240,8 @@ class Grid:
     """A cell grid over the neighbour set of one cloud (ps_grid_create / ps_grid_build)."""
 
     def __init__(self, n_max: int, cell_scale: float = 1.0, dense_min: int = 0, split: bool = False):
-        """cell_scale: cell edge / r_cut (>= 1: 27-cell search; [0.5, 1): 125-cell search).
+        """cell_scale: cell edge / r_cut (>= 1: 27-cell search; [0.5, 1): 125-cell search; [1/3, 0.5): 343
+        cells less the far corners that cannot hold a pair within r_cut).
         dense_min: cells with at least this many centrals use the shared-memory staged kernel (0: never).
         split: run the exact query in passes where it applies (near-radius kNN with a full-radius
         fallback, RDF over unordered pairs); same results (see ps_grid_opts.split)."""
@@ -249,6 +250,9 @@ class Grid:
         _check(lib().ps_grid_create(int(n_max), ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
         self.n_max = int(n_max)
+        self.cell_scale = float(np.float32(cell_scale if cell_scale else 1.0))
+        # cells searched around a cell along each axis (the library's rule)
+        self.stencil = 1 if self.cell_scale >= 1.0 else (2 if self.cell_scale >= 0.5 else 3)
         self._refs = ()
 
     @property

@@ -5,7 +5,8 @@ the cloud (density, type fractions) and on the query (r_max, k):
 
 * cell_scale: cell edge / r_cut.  1.0 searches the 27 cells around a cell;
   0.5 (or 0.75) searches the 125 cells within two half-size cells, which tests
-  ~40 % fewer candidates but spreads the centrals over more, smaller work items.
+  ~40 % fewer candidates but spreads the centrals over more, smaller work items;
+  1/3 searches 311 of the 343 cells within three cells (another ~25 % fewer).
 * dense_min: cells with at least this many centrals are handled by one CTA
   (8 warps) that stages the neighbour cells in shared memory with bulk copies;
   0 keeps every cell on the warp kernel (one warp per 32 centrals).
@@ -25,7 +26,7 @@ import math
 import os
 
 # (cell_scale, dense_min[, split])
-CANDIDATES = ((1.0, 0), (0.75, 0), (0.5, 0), (1.0, 128), (0.5, 0, 1))
+CANDIDATES = ((1.0, 0), (0.75, 0), (0.5, 0), (1.0, 128), (0.5, 0, 1), (1 / 3, 0, 1))
 
 _cache: dict = {}
 

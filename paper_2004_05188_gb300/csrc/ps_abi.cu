@@ -118,20 +118,20 @@ int ps_grid_create(int64_t n_max, const ps_grid_opts* opts, ps_grid** out) {
     if (opts->cell_scale != 0.0f) cell_scale = opts->cell_scale;
     if (opts->struct_size >= offsetof(ps_grid_opts, block) + sizeof(uint32_t)) block = opts->block;
   }
-  if (!(cell_scale >= 0.5f) || !std::isfinite(cell_scale))
-    return fail(PS_ERR_INVALID_ARG, "cell_scale must be >= 0.5");
+  if (!(cell_scale >= kMinCellScale) || !std::isfinite(cell_scale))
+    return fail(PS_ERR_INVALID_ARG, "cell_scale must be >= 1/3");
   ps_grid* g = new (std::nothrow) ps_grid();
   if (!g) return fail(PS_ERR_OOM, "host allocation failed");
   g->n_max = n_max > 0 ? n_max : 1;
   g->cell_scale = cell_scale;
-  g->stencil = cell_scale >= 1.0f ? 1 : 2;
+  g->stencil = cell_scale >= 1.0f ? 1 : (cell_scale >= 0.5f ? 2 : 3);
   g->block = block;
   if (opts && opts->struct_size >= offsetof(ps_grid_opts, dense_min) + sizeof(uint32_t))
     g->dense_min = opts->dense_min ? opts->dense_min : 0xFFFFFFFFu;
   if (opts && opts->struct_size >= offsetof(ps_grid_opts, split) + sizeof(uint32_t)) g->split = opts->split != 0;
   // cells: a bounding-box grid at the cutoff needs ~n/100 cells for the clouds seen here; the
   // capacity leaves a wide margin (the cell edge grows past it, results do not change)
-  const int64_t cap0 = g->stencil == 2 ? g->n_max : g->n_max / 8;
+  const int64_t cap0 = g->stencil >= 2 ? g->n_max : g->n_max / 8;
   const int64_t cap = cap0 > 65536 ? cap0 : 65536;
   g->cell_cap = (uint32_t)(cap < (int64_t)1 << 31 ? cap : (int64_t)1 << 31);
   // scan tiles of 4096 cells or 4096 records (the central list's record compaction)

@@ -451,6 +451,8 @@ int ps_batch_create(const ps_dataset* ds, int n_ds, const ps_sweep* sw, ps_batch
   for (uint32_t q = 0; q < s.n_dsrf; ++q)
     if (std::isnan(s.dsrf_min[q]) || (q && !(s.dsrf_min[q] > s.dsrf_min[q - 1])))
       return fail(PS_ERR_INVALID_ARG, "ps_batch_create: dsrf_min must ascend");
+  if (s.cell_scale != 0.0f && !(s.cell_scale >= 0.5f))
+    return fail(PS_ERR_UNSUPPORTED, "ps_batch_create: cell_scale must be 0 (default) or >= 0.5");
   const uint32_t smem_rdf = s.n_pairs * s.n_dsrf * s.bins.n_bins;
   if (smem_rdf > 8192) return fail(PS_ERR_UNSUPPORTED, "ps_batch_create: pairs x thresholds x bins > 8192");
   ps_batch* b = new (std::nothrow) ps_batch();

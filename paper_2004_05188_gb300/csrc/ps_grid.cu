@@ -505,6 +505,9 @@ __device__ __forceinline__ void emit_items(const uint32_t (&v)[kScanItems], uint
                                            uint32_t cap, const uint32_t* __restrict__ nstart, int stencil, bool split,
                                            uint2* __restrict__ whi) {
   uint32_t n_front = 0, n_back = 0, n_hi = 0;
+  // the work-shape estimates count the candidates of at most 5 x 5 rows (the 7 x 7 rows of a
+  // three-cell stencil would double the loads of this scan for a heuristic)
+  stencil = stencil > 2 ? 2 : stencil;
   bool sparse[kScanItems];
   uint32_t lanes[kScanItems], cands[kScanItems];
   const uint32_t n_nbr = nstart != nullptr ? nstart[nc] : 0u;

@@ -11,6 +11,7 @@
 namespace ps {
 
 constexpr uint32_t kSoftFineMax = 8192;  // fine-grid bins of the smoothed RDF
+constexpr float kMinCellScale = 1.0f / 3.0f;  // cell edge / r_cut: stencils of at most 3 cells
 
 // ---------------------------------------------------------------------------
 // error reporting
@@ -291,6 +292,34 @@ __device__ __forceinline__ void dist2_x2(unsigned long long px, unsigned long lo
   f2_unpack(f2_mul(dz, dz), za, zb);
   d2a = __fadd_rn(__fadd_rn(xa, ya), za);
   d2b = __fadd_rn(__fadd_rn(xb, yb), zb);
+}
+
+// Run table of a warp: run(r, src, len) for r < n_runs (up to 64, in rounds of 32 lanes), the
+// sources rsrc[r] and the prefix rpre[r + 1] of the lengths (rpre[0] = 0), so that the runs read
+// as one concatenated candidate list.  Returns the total length (every lane).
+template <class R>
+__device__ __forceinline__ uint32_t run_table(uint32_t lane, int n_runs, uint32_t* rsrc, uint32_t* rpre, R&& run) {
+  __syncwarp();
+  uint32_t total = 0;
+  for (int h = 0; h < n_runs; h += 32) {
+    const uint32_t r = (uint32_t)h + lane;
+    uint32_t src = 0, len = 0;
+    if (r < (uint32_t)n_runs) run(r, src, len);
+    uint32_t pre = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= (uint32_t)o) pre += y;
+    }
+    if (r < (uint32_t)n_runs) {
+      rsrc[r] = src;
+      rpre[r + 1] = total + pre;
+    }
+    total += __shfl_sync(0xffffffffu, pre, 31);
+  }
+  if (lane == 0) rpre[0] = 0;
+  __syncwarp();
+  return total;
 }
 
 // ---------------------------------------------------------------------------

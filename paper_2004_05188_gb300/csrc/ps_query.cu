@@ -31,7 +31,7 @@
 
 namespace ps {
 
-constexpr int kMaxRuns = 25;  // (2 * stencil + 1)^2 for stencil <= 2
+constexpr int kMaxRuns = 49;  // (2 * stencil + 1)^2 for stencil <= 3
 
 struct QueryArgs {
   const float4* nrec;
@@ -68,6 +68,10 @@ struct QueryArgs {
   // bin lookup table (lut_shift = 0: none): cell c covers the float32 bit patterns
   // [(lut_base + c) << lut_shift, (lut_base + c + 1) << lut_shift), at most one interior edge each
   uint32_t lut_shift, lut_base, lut_n;
+  // half-width of each stencil row (dy, dz), at [(dz + s) (2s + 1) + dy + s]: the row's cells
+  // cx - w .. cx + w can hold a record within r_cut of the cell's records, the others cannot
+  // (-1: none); w = s unless the cell is small against r_cut (see row_widths)
+  int8_t row_w[kMaxRuns];
 };
 
 template <int K>
@@ -324,14 +328,35 @@ __device__ __forceinline__ void add_pair_counters(const QueryArgs& a, uint64_t b
 }
 
 // Rows of the stencil, nearest first: (dy, dz) ordered by dy^2 + dz^2 (the first 9 entries are
-// the 3 x 3 rows of the 27-cell stencil).  Walking the central row first lets the k-th distance
-// of every central settle early, so later candidates rarely enter the top-k lists.
-__constant__ signed char c_row_dy[kMaxRuns] = {0, -1, 1, 0, 0, -1, 1, -1, 1, -2, 2, 0, 0,
-                                               -2, 2, -2, 2, -1, 1, -1, 1, -2, 2, -2, 2};
-__constant__ signed char c_row_dz[kMaxRuns] = {0, 0, 0, -1, 1, -1, -1, 1, 1, 0, 0, -2, 2,
-                                               -1, -1, 1, 1, -2, -2, 2, 2, -2, -2, 2, 2};
+// the 3 x 3 rows of the 27-cell stencil, the first 25 the 5 x 5 rows).  Walking the central row
+// first lets the k-th distance of every central settle early, so later candidates rarely enter
+// the top-k lists.
+__constant__ signed char c_row_dy[kMaxRuns] = {0, -1, 1, 0, 0, -1, 1, -1, 1, -2, 2, 0, 0, -2, 2, -2, 2,
+                                               -1, 1, -1, 1, -2, 2, -2, 2, 0, 0, -3, 3, -1, 1, -1, 1,
+                                               -3, 3, -3, 3, -2, 2, -2, 2, -3, 3, -3, 3, -3, 3, -3, 3};
+__constant__ signed char c_row_dz[kMaxRuns] = {0, 0, 0, -1, 1, -1, -1, 1, 1, 0, 0, -2, 2, -1, -1, 1, 1,
+                                               -2, -2, 2, 2, -2, -2, 2, 2, -3, 3, 0, 0, -3, -3, 3, 3,
+                                               -1, -1, 1, 1, -3, -3, 3, 3, -2, -2, 2, 2, -3, -3, 3, 3};
 
-// cell c -> run r of its stencil: the x-contiguous records of cells (cx-s .. cx+s, cy+dy, cz+dz)
+__device__ __forceinline__ int row_width(const QueryArgs& a, int dy, int dz) {
+  const int s = a.stencil;
+  return a.row_w[(dz + s) * (2 * s + 1) + dy + s];
+}
+
+// x-run of cells cx - w .. cx + w (clipped to the grid) of row (y, z): its records
+__device__ __forceinline__ void row_run(const QueryArgs& a, const Geo& ng, uint32_t cx, int y, int z, int w,
+                                        uint32_t& src, uint32_t& len) {
+  src = 0;
+  len = 0;
+  if (w < 0 || y < 0 || z < 0 || y >= (int)ng.dims[1] || z >= (int)ng.dims[2]) return;
+  const uint32_t xlo = cx >= (uint32_t)w ? cx - w : 0;
+  const uint32_t xhi = cx + w < ng.dims[0] ? cx + w : ng.dims[0] - 1;
+  const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+  src = a.nstart[row + xlo];
+  len = a.nstart[row + xhi + 1] - src;
+}
+
+// cell c -> run r of its stencil: the x-contiguous records of cells (cx-w .. cx+w, cy+dy, cz+dz)
 __device__ __forceinline__ void cell_run(const QueryArgs& a, const Geo& ng, uint32_t c, uint32_t r, uint32_t& src,
                                          uint32_t& len) {
   const int s = a.stencil, w = 2 * s + 1;
@@ -339,14 +364,8 @@ __device__ __forceinline__ void cell_run(const QueryArgs& a, const Geo& ng, uint
   src = 0;
   len = 0;
   if ((int)r >= w * w) return;
-  const int y = (int)cy + c_row_dy[r], z = (int)cz + c_row_dz[r];
-  if (y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2]) {
-    const uint32_t xlo = cx >= (uint32_t)s ? cx - s : 0;
-    const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
-    const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
-    src = a.nstart[row + xlo];
-    len = a.nstart[row + xhi + 1] - src;
-  }
+  const int dy = c_row_dy[r], dz = c_row_dz[r];
+  row_run(a, ng, cx, (int)cy + dy, (int)cz + dz, row_width(a, dy, dz), src, len);
 }
 
 __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(~0u)); }
@@ -400,22 +419,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.cstart[c] + first;
     // run table: sources and prefix counts of the candidate runs
-    uint32_t src = 0, len = 0;
-    cell_run(a, ng, c, lane, src, len);
-    uint32_t pre = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
-      if (lane >= (uint32_t)o) pre += y;
-    }
-    const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
-    __syncwarp();
-    if (lane < (uint32_t)n_runs) {
-      rsrc[lane] = src;
-      rpre[lane + 1] = pre;
-    }
-    if (lane == 0) rpre[0] = 0;
-    __syncwarp();
+    const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre,
+                                      [&](uint32_t r, uint32_t& src, uint32_t& len) { cell_run(a, ng, c, r, src, len); });
 
     // record at virtual candidate position pos (runs concatenated); rr is a run hint, nondecreasing in pos
     auto fetch = [&](uint32_t pos, int& rr) -> float4 {
@@ -646,19 +651,16 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         const float4 p = __ldg(a.crec + cl_rec[r0 + lane]);
         const uint32_t pidx = __float_as_uint(p.w);
         const uint32_t cx = ce % ng.dims[0], cy = (ce / ng.dims[0]) % ng.dims[1], cz = ce / (ng.dims[0] * ng.dims[1]);
-        const uint32_t xlo = cx >= (uint32_t)st ? cx - st : 0;
-        const uint32_t xhi = cx + st < ng.dims[0] ? cx + st : ng.dims[0] - 1;
-        const int ylo = max((int)cy - st, 0), yhi = min((int)cy + st, (int)ng.dims[1] - 1);
-        const int zlo = max((int)cz - st, 0), zhi = min((int)cz + st, (int)ng.dims[2] - 1);
         float top[KK];
 #pragma unroll
         for (int t = 0; t < KK; ++t) top[t] = INFINITY;
         uint32_t within = 0;
-        for (int z = zlo; z <= zhi; ++z)
-          for (int y = ylo; y <= yhi; ++y) {
-            const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
-            const uint32_t j1 = a.nstart[row + xhi + 1];
-            for (uint32_t j = a.nstart[row + xlo]; j < j1; ++j) {
+        for (int dz = -st; dz <= st; ++dz)
+          for (int dy = -st; dy <= st; ++dy) {
+            uint32_t j0 = 0, nj = 0;
+            row_run(a, ng, cx, (int)cy + dy, (int)cz + dz, row_width(a, dy, dz), j0, nj);
+            const uint32_t j1 = j0 + nj;
+            for (uint32_t j = j0; j < j1; ++j) {
               const float4 q = __ldg(a.nrec + j);
               const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
               if (d2 < erange && __float_as_uint(q.w) != pidx) {
@@ -830,15 +832,16 @@ __global__ void __launch_bounds__(256) k_query_cta(const QueryArgs a) {
 // record), and d2_ij == d2_ji bit for bit (x_j - x_i == -(x_i - x_j) in IEEE arithmetic), so
 // each pair is tested once, from the lower of its two cells: the half of the stencil with
 // (dz > 0) or (dz == 0 and dy > 0) or (dz == dy == 0 and dx > 0), plus the pairs i < j inside
-// the cell.  A warp takes 32 cells at a time, and for each non-empty cell runs its records (32
-// at a time) as lanes against the half stencil's records, staged 32 at a time and tested two
-// at a time with packed float32 math; the hits (d2, weight) are compacted into a warp list and
-// binned into the warp's 32-bit shared row by all lanes.  The flags come from the central
-// prefix pfx over the records (c_j = pfx[j+1] - pfx[j]).
+// the cell.  A warp takes 32 cells at a time, and for each non-empty cell tests the half
+// stencil's records (the lanes, 32 per load) against the cell's records (staged in shared
+// memory, read by all lanes at once, two at a time with packed float32 math); the hits (d2,
+// weight) are compacted into a warp list and binned into the warp's 32-bit shared row by all
+// lanes.  The flags come from the central prefix pfx over the records (c_j = pfx[j+1] - pfx[j]).
 // ---------------------------------------------------------------------------
 
-// half-stencil run r of cell c: full x-runs of the rows with dz > 0 (all dy) and of the rows
-// dz == 0, dy > 0; the row dz == dy == 0 from cx + 1 on.  (2s+1)s + s + 1 runs.
+// half-stencil run r of cell c: the x-runs of the rows with dz > 0 (all dy) and of the rows
+// dz == 0, dy > 0 (each over its width, see row_width); the row dz == dy == 0 from cx + 1 on.
+// (2s+1)s + s + 1 runs.
 __device__ __forceinline__ void sym_run(const QueryArgs& a, const Geo& ng, uint32_t c, uint32_t r, uint32_t& src,
                                         uint32_t& len) {
   const int s = a.stencil, W = 2 * s + 1;
@@ -846,7 +849,6 @@ __device__ __forceinline__ void sym_run(const QueryArgs& a, const Geo& ng, uint3
   src = 0;
   len = 0;
   int dy, dz;
-  uint32_t xlo = cx >= (uint32_t)s ? cx - s : 0;
   if ((int)r < W * s) {
     dz = 1 + (int)r / W;
     dy = (int)r % W - s;
@@ -854,28 +856,29 @@ __device__ __forceinline__ void sym_run(const QueryArgs& a, const Geo& ng, uint3
     dz = 0;
     dy = 1 + ((int)r - W * s);
   } else if ((int)r == W * s + s) {
-    dz = 0;
-    dy = 0;
-    xlo = cx + 1;
+    // own row, the cells after c: cx + 1 .. cx + s
+    const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
+    if (cx + 1 <= xhi) {
+      const uint32_t row = (cz * ng.dims[1] + cy) * ng.dims[0];
+      src = a.nstart[row + cx + 1];
+      len = a.nstart[row + xhi + 1] - src;
+    }
+    return;
   } else {
     return;
   }
-  const uint32_t xhi = cx + s < ng.dims[0] ? cx + s : ng.dims[0] - 1;
-  const int y = (int)cy + dy, z = (int)cz + dz;
-  if (y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2] && xlo <= xhi) {
-    const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
-    src = a.nstart[row + xlo];
-    len = a.nstart[row + xhi + 1] - src;
-  }
+  row_run(a, ng, cx, (int)cy + dy, (int)cz + dz, row_width(a, dy, dz), src, len);
 }
+
+constexpr uint32_t kSymGroup = 64;  // records of a cell staged at a time by the symmetric pass
 
 __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   griddep_wait();
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ float4 s_buf[8][32];
-  __shared__ uint32_t s_hits[8][32 * kHalf + 32];  // per warp: one half-batch's hits + a trash row: the bits
-                                                  // of d2, the sign bit set for weight 2
+  __shared__ float4 s_grp[8][kSymGroup];          // per warp: the cell's records as interleaved pairs
+  __shared__ uint32_t s_hits[8][32 * kHalf + 32];  // per warp: the hits of 8 record pairs + a trash row: the
+                                                  // bits of d2, the sign bit set for weight 2
   __shared__ uint32_t s_rsrc[8][kMaxRuns], s_rpre[8][kMaxRuns + 1];
   Hist<true> H;
   H.init(a, smem, 0, true);
@@ -887,7 +890,7 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   const int s = a.stencil, n_runs = (2 * s + 1) * s + s + 1;
   uint64_t my_binned = 0;
   uint32_t my_below = 0;
-  float* bf = reinterpret_cast<float*>(s_buf[w]);
+  float* gf = reinterpret_cast<float*>(s_grp[w]);
   uint32_t* wlist = s_hits[w];
   uint32_t* rsrc = s_rsrc[w];
   uint32_t* rpre = s_rpre[w];
@@ -911,106 +914,94 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
       const uint32_t c = base + (uint32_t)src_lane;
       const uint32_t a0 = __shfl_sync(0xffffffffu, s0, src_lane), a1 = __shfl_sync(0xffffffffu, s1, src_lane);
       // run table of the half stencil
-      uint32_t src = 0, len = 0;
-      sym_run(a, ng, c, lane, src, len);
-      uint32_t pre = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= (uint32_t)o) pre += y;
-      }
-      const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
-      __syncwarp();
-      if (lane < (uint32_t)n_runs) {
-        rsrc[lane] = src;
-        rpre[lane + 1] = pre;
-      }
-      if (lane == 0) rpre[0] = 0;
-      __syncwarp();
+      const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre,
+                                        [&](uint32_t r, uint32_t& src, uint32_t& len) { sym_run(a, ng, c, r, src, len); });
 
-      // candidate at virtual position pos (runs concatenated); .w = E[nb] for a central, -1 otherwise
-      auto fetch = [&](uint32_t pos, int& rr) -> float4 {
-        if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, -1.f);
-        while (pos >= rpre[rr + 1]) ++rr;
-        const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
-        float4 q = __ldg(a.nrec + j);
-        q.w = __ldg(a.pfx + j + 1) > __ldg(a.pfx + j) ? E_max : -1.f;
-        return q;
-      };
-
+      // pairs inside the cell: record i (a lane) with j in (i, a1), each lane on its own (a small
+      // share of the pairs)
       for (uint32_t i0 = a0; i0 < a1; i0 += 32) {
-        // L lanes per record when the chunk holds few records (a cell's last chunk, sparse cells):
-        // lane sub of a record tests the candidate pairs t = sub mod L
-        const uint32_t m = min(32u, a1 - i0);
-        const uint32_t L = item_lanes(m < 4u ? 4u : m);
-        const uint32_t lg = L == 8u ? 3u : (L == 4u ? 2u : (L == 2u ? 1u : 0u));
-        const uint32_t sub = lane & (L - 1u), n_it = 8u >> lg;
-        const uint32_t i = i0 + (lane >> lg);
-        const bool valid = (lane >> lg) < m;
-        float4 p = make_float4(INFINITY, INFINITY, INFINITY, 0.f);  // lanes without a record never hit
-        float ci = 0.f;
-        if (valid) {
-          p = __ldg(a.nrec + i);
-          ci = (float)(__ldg(a.pfx + i + 1) - __ldg(a.pfx + i));
-        }
-        // a pair counts when either end is central: the range is max(lane's, candidate's), each
-        // E[nb] for a central and -1 otherwise; weight 2 (sign bit) when both are
-        const float elane = ci > 0.f ? E_max : -1.f;
-        const uint32_t w2lane = ci > 0.f ? 0x80000000u : 0u;
-        // pairs inside the cell: j in (i, a1), each lane on its own (a small share of the pairs)
-        {
-          uint32_t inc = 0;
-          if (valid) {
-            const bool big = a1 - a0 > (1u << 20);  // per-lane increments stay far below the row's 2^32
-            for (uint32_t j = i + 1 + sub; j < a1; j += L) {
-              const float4 q = __ldg(a.nrec + j);
-              const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-              const uint32_t wt = (uint32_t)ci + (__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
-              if (d2 < E_max && wt) {
-                if (big) {
-                  H.pair_global(a, d2, wt, my_binned, my_below);
-                } else {
-                  H.pair_w(d2, wt, my_below);
-                  inc += wt;
-                }
+        const uint32_t i = i0 + lane;
+        uint32_t inc = 0;
+        if (i < a1) {
+          const float4 p = __ldg(a.nrec + i);
+          const uint32_t ci = __ldg(a.pfx + i + 1) - __ldg(a.pfx + i);
+          const bool big = a1 - a0 > (1u << 20);  // per-lane increments stay far below the row's 2^32
+          for (uint32_t j = i + 1; j < a1; ++j) {
+            const float4 q = __ldg(a.nrec + j);
+            const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+            const uint32_t wt = ci + (__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+            if (d2 < E_max && wt) {
+              if (big) {
+                H.pair_global(a, d2, wt, my_binned, my_below);
+              } else {
+                H.pair_w(d2, wt, my_below);
+                inc += wt;
               }
             }
           }
-          wcount += __reduce_add_sync(0xffffffffu, inc);
-          if (wcount >= (1ull << 31)) {
-            H.flush_warp(a);
-            wcount = 0;
+        }
+        wcount += __reduce_add_sync(0xffffffffu, inc);
+        if (wcount >= (1ull << 31)) {
+          H.flush_warp(a);
+          wcount = 0;
+        }
+      }
+      if (n_cand == 0) continue;
+
+      // the half stencil: the candidates are the lanes (32 per coalesced load, each in registers),
+      // the cell's records are staged in shared memory (up to kSymGroup at a time, as interleaved
+      // pairs xa xb ya yb za zb ea eb) and read by every lane at once, two per packed test; a
+      // record's e (and a candidate's) is E[nb] for a central and -1 otherwise, the range of a
+      // pair max(e_rec, e_cand), weight 2 (sign bit) when both are central.  The lanes stay busy
+      // whatever the cell's record count.
+      for (uint32_t g0 = a0; g0 < a1; g0 += kSymGroup) {
+        const uint32_t m = min(kSymGroup, a1 - g0), n_pr = (m + 1) >> 1;
+        __syncwarp();
+#pragma unroll
+        for (uint32_t h = 0; h < kSymGroup; h += 32) {
+          const uint32_t r = h + lane;
+          if (r < 2 * n_pr) {
+            float4 q = make_float4(INFINITY, INFINITY, INFINITY, -1.f);  // the pad of an odd group never hits
+            if (r < m) {
+              q = __ldg(a.nrec + g0 + r);
+              q.w = __ldg(a.pfx + g0 + r + 1) > __ldg(a.pfx + g0 + r) ? E_max : -1.f;
+            }
+            float* d = gf + (r >> 1) * 8 + (r & 1);
+            d[0] = q.x, d[2] = q.y, d[4] = q.z, d[6] = q.w;
           }
         }
-        // the half stencil: 32 candidates per coalesced load, staged as 16 interleaved pairs
-        // (xa xb ya yb za zb ca cb), tested two at a time
-        const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
+        __syncwarp();
         int rr = 0;
-        float4 nxt = fetch(lane, rr);
+        auto fetch = [&](uint32_t pos) -> float4 {
+          if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, -1.f);
+          while (pos >= rpre[rr + 1]) ++rr;
+          const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
+          float4 q = __ldg(a.nrec + j);
+          q.w = __ldg(a.pfx + j + 1) > __ldg(a.pfx + j) ? E_max : -1.f;
+          return q;
+        };
+        float4 nxt = fetch(lane);
         for (uint32_t b = 0; b < n_cand; b += 32) {
-          __syncwarp();
-          {
-            float* d = bf + (lane >> 1) * 8 + (lane & 1);
-            d[0] = nxt.x, d[2] = nxt.y, d[4] = nxt.z, d[6] = nxt.w;
-          }
-          __syncwarp();
-          nxt = fetch(b + 32 + lane, rr);
-#pragma unroll 1
-          for (int half = 0; half < 2; ++half) {
+          const float4 q = nxt;
+          nxt = fetch(b + 32 + lane);
+          const unsigned long long qx = f2_pack(q.x, q.x), qy = f2_pack(q.y, q.y), qz = f2_pack(q.z, q.z);
+          const float eq = q.w;
+          const uint32_t w2q = eq > 0.f ? 0x80000000u : 0u;
+          for (uint32_t k0 = 0; k0 < n_pr; k0 += 8) {
+            const uint32_t k1 = min(n_pr, k0 + 8);
             uint32_t nh = 0;  // hits in the warp list (uniform)
 #pragma unroll 2
-            for (uint32_t u = 0; u < n_it; ++u) {
-              const uint32_t t = 8 * half + u * L + sub;
-              const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(bf)[2 * t];
-              const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(bf)[2 * t + 1];
+            for (uint32_t k = k0; k < k1; ++k) {
+              const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(gf)[2 * k];
+              const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(gf)[2 * k + 1];
               float d2a, d2b;
-              dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
+              dist2_x2(xy.x, xy.y, zw.x, qx, qy, qz, d2a, d2b);
               float ea, eb;
               f2_unpack(zw.y, ea, eb);
-              const bool ha = d2a < fmaxf(elane, ea);
-              const bool hb = d2b < fmaxf(elane, eb);
-              const uint32_t va = __float_as_uint(d2a) | (~__float_as_uint(ea) & w2lane);
-              const uint32_t vb = __float_as_uint(d2b) | (~__float_as_uint(eb) & w2lane);
+              const bool ha = d2a < fmaxf(eq, ea);
+              const bool hb = d2b < fmaxf(eq, eb);
+              const uint32_t va = __float_as_uint(d2a) | (~__float_as_uint(ea) & w2q);
+              const uint32_t vb = __float_as_uint(d2b) | (~__float_as_uint(eb) & w2q);
               // every lane stores (no branch): a hit at its compacted slot, a miss in the trash row
               const uint32_t ba = __ballot_sync(0xffffffffu, ha);
               wlist[ha ? nh + __popc(ba & lt) : 32 * kHalf + lane] = va;
@@ -1114,6 +1105,25 @@ static void choose_lut(ps_bins bins, QueryArgs& qa) {
   }
 }
 
+// Row widths of a stencil of s cells for cells of edge h >= r_cut * cs * (1 + 2^-10) (plus the
+// grid's rounding margin extent * 2^-20, which covers the float32 rounding of the cell index).
+// Two points whose cells are |d| >= 2 apart along an axis are more than (|d| - 1) r_cut cs apart
+// along it, so cell offset (dx, dy, dz) can hold a pair within r_cut only if
+// sum_i max(0, |d_i| - 1)^2 (cs (1 + 2^-10))^2 < 1; the test keeps a further 2^-20 margin.
+// Only stencils of three cells (cs < 1/2) lose cells: their 8 x 3 far corners of each octant.
+static void row_widths(int s, double cs, int8_t* w) {
+  const int W = 2 * s + 1;
+  const double f = cs * (1.0 + 1.0 / 1024.0), lim = (1.0 + 1.0 / 1048576.0) * (1.0 + 1.0 / 1048576.0);
+  auto m2 = [](int d) { const int m = d < 0 ? -d - 1 : d - 1; return m > 0 ? (double)(m * m) : 0.0; };
+  for (int dz = -s; dz <= s; ++dz)
+    for (int dy = -s; dy <= s; ++dy) {
+      int width = -1;
+      for (int dx = 0; dx <= s; ++dx)
+        if ((m2(dx) + m2(dy) + m2(dz)) * f * f < lim) width = dx;
+      w[(dz + s) * W + dy + s] = (int8_t)width;
+    }
+}
+
 int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_bins bins,
               const uint32_t* ks, uint32_t n_k, uint64_t* d_rdf, uint64_t* d_knn, uint64_t* d_meta, float* d_kth,
               uint32_t* d_nwithin, cudaStream_t s) {
@@ -1130,6 +1140,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.work_cap = g->item_cap;
   qa.cgeo = g->ctr.geo;
   qa.stencil = g->stencil;
+  row_widths(g->stencil, g->cell_scale, qa.row_w);
   qa.r0 = bins.r0;
   qa.dr = bins.dr;
   qa.n_bins = bins.n_bins;
@@ -1172,7 +1183,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   const uint32_t smem_warp = smem_layout(bins.n_bins, n_k, rdf, 0, true, qa.lut_n).total;
   bool subset = !g->pack_type;
   for (int w = 0; w < 4; ++w) subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
-  if (g->split && subset && rdf && d_nwithin == nullptr && g->stencil == 2 && g->dense_min == 0xFFFFFFFFu) {
+  if (g->split && subset && rdf && d_nwithin == nullptr && g->stencil >= 2 && g->dense_min == 0xFFFFFFFFu) {
     // the query in passes: (1) kNN within the cell edge r_cut * cell_scale (27 cells of the
     // grid), centrals with fewer than k_need neighbours there marked; (2) the full-radius kNN
     // of the marked centrals; (3) the RDF over unordered pairs
@@ -1183,6 +1194,7 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
       const float Emax = (float)(e * e), Ek = (float)(rk * rk);
       qn.emax_near = Ek < Emax ? Ek : Emax;
       qn.stencil = 1;
+      row_widths(1, 1.0, qn.row_w);
       qn.need = g->sel;  // free between a build and the next one (the counting sort's index list)
       rc = dispatch_k<false>(g, qn, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
       if (rc) return rc;

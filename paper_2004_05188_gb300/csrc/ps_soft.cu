@@ -35,7 +35,7 @@
 
 namespace ps {
 
-constexpr int kSoftRuns = 25;
+constexpr int kSoftRuns = 49;  // (2 * stencil + 1)^2 for stencil <= 3
 
 struct SoftArgs {
   // owners (one lane per record) and their work items
@@ -136,25 +136,12 @@ __device__ __forceinline__ void soft_items_listed(const SoftArgs& a, float* bf, 
     const uint2 it = work_item(a.oitem, a.ocap, n_front, item);
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.ostart[c] + first;
-    uint32_t src = 0, len = 0;
-    if (SYM)
-      soft_half_run(a, ng, c, lane, src, len);
-    else
-      soft_run(a, ng, c, lane, src, len);
-    uint32_t pre = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
-      if (lane >= (uint32_t)o) pre += y;
-    }
-    const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
-    __syncwarp();
-    if (lane < (uint32_t)n_runs) {
-      rsrc[lane] = src;
-      rpre[lane + 1] = pre;
-    }
-    if (lane == 0) rpre[0] = 0;
-    __syncwarp();
+    const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre, [&](uint32_t r, uint32_t& src, uint32_t& len) {
+      if (SYM)
+        soft_half_run(a, ng, c, r, src, len);
+      else
+        soft_run(a, ng, c, r, src, len);
+    });
     const uint32_t a1 = SYM ? a.ostart[c + 1] : 0u;  // end of the owner's cell
     item_hook(cnt, n_cand + (SYM ? a1 - c0 : 0u));
     const bool valid = lane < cnt;
@@ -261,22 +248,9 @@ __device__ __forceinline__ void soft_items_owned(const SoftArgs& a, float* bf, u
     const uint2 it = work_item(a.oitem, a.ocap, n_front, item);
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.ostart[c] + first;
-    uint32_t src = 0, len = 0;
-    soft_run(a, ng, c, lane, src, len);
-    uint32_t pre = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
-      if (lane >= (uint32_t)o) pre += y;
-    }
-    const uint32_t n_cand = __shfl_sync(0xffffffffu, pre, 31);
-    __syncwarp();
-    if (lane < (uint32_t)n_runs) {
-      rsrc[lane] = src;
-      rpre[lane + 1] = pre;
-    }
-    if (lane == 0) rpre[0] = 0;
-    __syncwarp();
+    const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre, [&](uint32_t r, uint32_t& src, uint32_t& len) {
+      soft_run(a, ng, c, r, src, len);
+    });
     const bool valid = lane < cnt;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     float c_own = 0.f;

@@ -13,8 +13,19 @@ def _cells_np(P, org, inv_h, dims):
     return np.clip(u, 0, np.array(dims) - 1)
 
 
-@pytest.mark.parametrize("stencil,h", [(1, 2.0), (2, 1.0)])
-def test_candidate_tests_brute_force(stencil, h):
+def _kept(dc, cs):
+    """Cell offsets the exact query searches: the gap (|d| - 1 cells per axis, on the cell-edge
+    bound r_cut cs (1 + 2^-10)) below r_cut (1 + 2^-20); every offset when cs is None."""
+    if cs is None:
+        return np.ones(dc.shape[:-1], bool)
+    m = np.maximum(np.abs(dc) - 1, 0).astype(np.float64)
+    f = float(np.float32(cs)) * (1 + 2.0**-10)
+    return (m**2).sum(axis=-1) * f * f < (1 + 2.0**-20) ** 2
+
+
+@pytest.mark.parametrize("stencil,h,cs", [(1, 2.0, None), (2, 1.0, None), (2, 1.0, 0.5), (2, 1.0, 0.75),
+                                          (3, 0.7, 1 / 3)])
+def test_candidate_tests_brute_force(stencil, h, cs):
     rng = np.random.default_rng(7)
     n = 3000
     xyz = (rng.random((n, 3)) * np.array([9.0, 7.0, 11.0])).astype(np.float32)
@@ -24,12 +35,14 @@ def test_candidate_tests_brute_force(stencil, h):
     dims = tuple(int(np.floor((xyz[:, a].max() - org[a]) / h)) + 1 for a in range(3))
     info = dict(dims=dims, origin=tuple(float(v) for v in org), cell=h, n_cells=dims[0] * dims[1] * dims[2])
     got = bench.candidate_tests(torch.from_numpy(xyz), torch.from_numpy(t), torch.from_numpy(d), [1], [1, 2], 1.0,
-                                info, stencil)
+                                info, stencil, cell_scale=cs)
     inv_h = np.float32(1.0 / h)
     cn = _cells_np(xyz[np.isin(t, [1, 2])], org, inv_h, dims)
     cc = _cells_np(xyz[(t == 1) & (d >= 1.0)], org, inv_h, dims)
-    want = sum(int((np.abs(cn - c).max(axis=1) <= stencil).sum()) for c in cc)
+    want = sum(int(((np.abs(cn - c).max(axis=1) <= stencil) & _kept(cn - c, cs)).sum()) for c in cc)
     assert got == want > 0
+    if cs is not None and cs < 1 / stencil + 0.1:
+        assert got < sum(int((np.abs(cn - c).max(axis=1) <= stencil).sum()) for c in cc) or stencil == 2
 
 
 def test_stored_traffic_guard():
@@ -114,21 +127,34 @@ def test_needle_sample_is_the_middle_of_the_needle(orc, spec, monkeypatch):
     assert got == int((d[off[lo]:off[hi]] >= 0.5).sum())
 
 
-def test_symmetric_pass_test_count_brute_force():
+@pytest.mark.parametrize("stencil,h,cs", [(2, 1.0, 0.5), (3, 0.7, 1 / 3)])
+def test_symmetric_pass_test_count_brute_force(stencil, h, cs):
     """The symmetric RDF pass tests every unordered pair of records whose cells are within the
-    stencil once: (sum over records of their stencil population - n) / 2, by brute force."""
+    searched stencil once: (sum over records of their stencil population - n) / 2, by brute force."""
     rng = np.random.default_rng(8)
     n = 2500
     xyz = (rng.random((n, 3)) * np.array([6.0, 5.0, 7.0])).astype(np.float32)
     t = rng.integers(0, 2, n).astype(np.uint8)
     d = np.full(n, np.nan, np.float32)  # no d_srf filter applies to the record count
-    h, stencil = 1.0, 2
     org = xyz.min(axis=0)
     dims = tuple(int(np.floor((xyz[:, a].max() - org[a]) / h)) + 1 for a in range(3))
     info = dict(dims=dims, origin=tuple(float(v) for v in org), cell=h, n_cells=dims[0] * dims[1] * dims[2])
     full = bench.candidate_tests(torch.from_numpy(xyz), torch.from_numpy(t), torch.from_numpy(d), "all", "all", 0.0,
-                                 info, stencil, all_records=True)
+                                 info, stencil, all_records=True, cell_scale=cs)
     c = _cells_np(xyz, org, np.float32(1.0 / h), dims)
-    cheb = np.abs(c[:, None, :] - c[None, :, :]).max(axis=2)
-    pairs = int(np.triu(cheb <= stencil, k=1).sum())
+    dc = c[:, None, :] - c[None, :, :]
+    near = (np.abs(dc).max(axis=2) <= stencil) & _kept(dc, cs)
+    pairs = int(np.triu(near, k=1).sum())
     assert (full - n) // 2 == pairs and (full - n) % 2 == 0
+
+
+def test_row_widths_rule():
+    """Half-size cells keep every cell of the 5 x 5 x 5 stencil; third-size cells drop the 4 far
+    corner cells of each octant (32 of 343); cells of 0.75 r_cut drop the rows (+-2, +-2) and the
+    ends of the rows with one offset of 2."""
+    assert bench.row_widths(2, 0.5) == [[2] * 5] * 5
+    w3 = bench.row_widths(3, 1 / 3)
+    assert sum(2 * w + 1 for row in w3 for w in row if w >= 0) == 343 - 32
+    assert w3[0][0] == 1 and w3[0][1] == 2 and w3[0][2] == 3 and w3[3][3] == 3
+    w = bench.row_widths(2, 0.75)
+    assert w[0][0] == -1 and w[4][4] == -1 and w[0][2] == 1 and w[1][0] == 1 and w[2][2] == 2

@@ -173,9 +173,13 @@ def test_extreme_clusters_split_lanes(ps, orc, spec):
         assert_same(gg, r, ks, per_central=True)
 
 
-@pytest.mark.parametrize("cell_scale,dense_min", [(1.0, 0), (1.0, 40), (0.5, 0), (0.5, 8), (0.7, 0), (1.3, 1)])
+@pytest.mark.parametrize("cell_scale,dense_min", [(1.0, 0), (1.0, 40), (0.5, 0), (0.5, 8), (0.7, 0), (0.75, 0),
+                                                  (0.75, 8), (1.3, 1), (1 / 3, 0), (1 / 3, 4), (0.4, 0)])
 def test_kernel_variants_stencils(ps, orc, spec, cell_scale, dense_min):
-    """27- and 125-cell stencils, warp kernel alone and with the CTA kernel taking the dense cells."""
+    """27-, 125- and 343-cell stencils (the last two less the cells that cannot hold a pair
+    within r_cut: the 8 corners at cell_scale 0.7, whole rows at 0.75, the 32 far corners at 1/3),
+    warp kernel alone (49 stencil rows in two run-table rounds at 1/3) and with the CTA kernel
+    taking the dense cells."""
     xyz, t, d = spec.cube(111, 12000, 7.5, (0.7, 0.2, 0.1))
     bins = (0.0, 0.02, 80)
     for ctr, nbr, dmin, ks in [("all", "all", 0.5, [1, 3, 12]), ([1], [1, 2], 0.0, [2]), ([0], "all", 1.0, [32])]:

@@ -55,7 +55,7 @@ def _check(orc, xyz, t, d, nbr, ctr, dmin, scale, G, h, gx, gs):
     return href, gref, gsref
 
 
-@pytest.mark.parametrize("scale,cell_scale", [(1.0, 1.0), (0.93, 1.0), (1.07, 0.5)])
+@pytest.mark.parametrize("scale,cell_scale", [(1.0, 1.0), (0.93, 1.0), (1.07, 0.5), (1.0, 1 / 3)])
 def test_soft_forward_and_adjoint_vs_fp64(ps, orc, spec, scale, cell_scale):
     xyz, t, d = spec.cube(201, 1500, 3.7, (0.7, 0.3))
     G = np.random.default_rng(11).standard_normal(BINS[2])

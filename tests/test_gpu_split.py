@@ -45,7 +45,7 @@ def test_poisson_cube_split(ps, orc, spec, n, L, seed):
     xyz, t, d = spec.cube(seed, n, L, (0.6, 0.3, 0.1))
     bins = (0.0, 0.02, 75)
     for ctr, nbr, dmin, ks in CASES:
-        for cs in (0.5, 0.75):
+        for cs in (0.5, 0.75, 1 / 3):
             g = run_gpu(ps, xyz, t, d, ctr, nbr, dmin, bins, ks, per_central="kth", cell_scale=cs, split=True)
             r = orc.spatstat(xyz, t, d, ctr, nbr, dmin, *bins, ks, per_central=True)
             assert_same(g, r, ks, per_central="kth")
@@ -62,13 +62,14 @@ def test_cylinder_200k_split_full_size(ps, orc, spec):
     assert_same(g, r, [1, 10], per_central=True)
 
 
-def test_needle_8m_sparse_types_split(ps, orc, spec):
-    """Sc-Sc: almost no Sc has 5 Sc neighbours within 1 nm, so nearly every central takes the
-    full-radius fallback."""
+@pytest.mark.parametrize("cell_scale", [0.5, 1 / 3])
+def test_needle_8m_sparse_types_split(ps, orc, spec, cell_scale):
+    """Sc-Sc: almost no Sc has 5 Sc neighbours within 1 nm (0.67 nm with third-size cells), so
+    nearly every central takes the full-radius fallback (49 stencil rows with third-size cells)."""
     xyz, t, d = spec.needle(spec.needle_8m_params())
     bins = ps.bins_from_spec(0.0, 0.01, 2.0)
     for ctr, nbr, ks in (([1], [1], [1, 5, 10]), ([2], [2], [1, 5, 10]), ([1], [1, 2], [2])):
-        g = run_gpu(ps, xyz, t, d, ctr, nbr, 2.0, bins, ks, per_central="kth", cell_scale=0.5, split=True)
+        g = run_gpu(ps, xyz, t, d, ctr, nbr, 2.0, bins, ks, per_central="kth", cell_scale=cell_scale, split=True)
         r = orc.spatstat(xyz, t, d, ctr, nbr, 2.0, *bins, ks, per_central=True)
         assert_same(g, r, ks, per_central="kth")
 
@@ -138,15 +139,15 @@ def test_bin_lookup_regimes(ps, orc, spec, bins):
         assert_same(g, r, [1, 4], per_central="kth")
 
 
-@pytest.mark.parametrize("rho", [3.0, 12.0, 33.0])
-def test_split_lane_chunks(ps, orc, spec, rho):
-    """Chunks of few records (sparse cells, a cell's last chunk past 32 records) give several
-    lanes to a record: 3, 12 and 33 ions per nm^3 on cells of ~1 nm^3 cover 8, 4, 2 and 1 lanes
-    per record."""
+@pytest.mark.parametrize("rho,cs", [(3.0, 0.5), (12.0, 0.5), (33.0, 0.5), (33.0, 1 / 3), (120.0, 1 / 3)])
+def test_split_lane_chunks(ps, orc, spec, rho, cs):
+    """Cells of few and of many records: 3, 12 and 33 ions per nm^3 on cells of ~1 nm^3 (items
+    of 8, 4, 2 and 1 lanes per central in the near pass, record groups of every size in the
+    symmetric pass), and third-size cells (~0.3 nm^3) at 33 and 120 ions per nm^3."""
     L = 9.0
     xyz, t, d = spec.cube(208, int(rho * L**3), L, (0.6, 0.4))
     bins = (0.0, 0.02, 100)
     for ctr, nbr, ks in (("all", "all", [1, 6]), ([1], [0, 1], [2]), ([0], [0], [])):
         r = orc.spatstat(xyz, t, d, ctr, nbr, 0.7, *bins, ks, per_central=True)
-        g = run_gpu(ps, xyz, t, d, ctr, nbr, 0.7, bins, ks, per_central="kth", cell_scale=0.5, split=True)
+        g = run_gpu(ps, xyz, t, d, ctr, nbr, 0.7, bins, ks, per_central="kth", cell_scale=cs, split=True)
         assert_same(g, r, ks, per_central="kth")
