@@ -25,7 +25,8 @@ def test_choose_keeps_default_within_margin():
 
 def test_tune_uses_runner_and_caches(tmp_path):
     calls = []
-    t = {(1.0, 0, 0): 3.0, (0.75, 0, 0): 2.5, (0.5, 0, 0): 1.0, (1.0, 128, 0): 4.0, (0.5, 0, 1): 0.6}
+    t = {(1.0, 0, 0): 3.0, (0.75, 0, 0): 2.5, (0.5, 0, 0): 1.0, (1.0, 128, 0): 4.0, (0.5, 0, 1): 0.6,
+         (1 / 3, 0, 1): 0.7}
 
     def runner(cs, dm, sp):
         calls.append((cs, dm, sp))
@@ -35,15 +36,15 @@ def test_tune_uses_runner_and_caches(tmp_path):
     r = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1",
                       cache_path=path)
     assert (r["cell_scale"], r["dense_min"], r["split"], r["cached"]) == (0.5, 0, 1, False)
-    assert len(calls) == 5
+    assert len(calls) == 6
     r2 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1")
-    assert r2["cached"] and len(calls) == 5
+    assert r2["cached"] and len(calls) == 6
     with open(path) as f:
         assert json.load(f)["k1"]["cell_scale"] == 0.5
     autotune._cache.clear()
     r3 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k1",
                        cache_path=path)
-    assert r3["cached"] and len(calls) == 5
+    assert r3["cached"] and len(calls) == 6
     # two-element candidates are (cell_scale, dense_min) with split off
     autotune._cache.clear()
     r4 = autotune.tune(None, None, None, "all", "all", 0.0, (0.0, 0.01, 200), [1], runner=runner, key="k2",
