@@ -802,7 +802,12 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
         "hbm_build": {"achieved": b_bytes / (b_ms * 1e-3) / 1e9 if b_ms > 0 else 0.0, "peak": hbm_peak,
                       "unit": "GB/s", "frac": (b_bytes / (b_ms * 1e-3) / 1e9) / hbm_peak if b_ms > 0 else None,
                       "kernels": list(BUILD_FAMS), "ms_per_step": b_ms / max(1, steps),
-                      "algorithmic_bytes_per_step": b_bytes / max(1, steps), "peak_source": hbm_src},
+                      "algorithmic_bytes_per_step": b_bytes / max(1, steps), "peak_source": hbm_src,
+                      "by_kernel": {f: {"ms_per_step": prof[f][1] / max(1, steps),
+                                        "gb_per_step": sum(algorithmic_bytes(f, st, c) for c in st["combos"]) / 1e9,
+                                        "frac": (sum(algorithmic_bytes(f, st, c) for c in st["combos"]) * steps
+                                                 / (prof[f][1] * 1e-3) / 1e9 / hbm_peak) if prof[f][1] > 0 else None}
+                                    for f in BUILD_FAMS}},
     }
 
 

@@ -111,7 +111,7 @@ struct SmemLayout {
   bool priv;
 };
 
-constexpr uint32_t kLutMax = 4096;  // entries of the bin lookup table (uint16)
+constexpr uint32_t kLutMax = 4096;  // entries of the bin lookup table (uint32)
 
 constexpr uint32_t kPrivBins = 512;  // up to this many bins each warp keeps its own 32-bit RDF row
 
@@ -123,7 +123,7 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_bins, uint32_t n_k,
   L.off_E = o;
   o += (n_bins + 1) * 4;
   L.off_lut = o;
-  o += rdf ? lut_n * 2 : 0;
+  o += rdf ? lut_n * 4 : 0;
   o = (o + 7u) & ~7u;
   L.off_rdf = o;
   o += rdf ? (L.priv ? 8 * n_bins * 4 : n_bins * 8) : 0;
@@ -147,18 +147,18 @@ struct Hist {
   bool priv;
   uint32_t* s_knn;            // per-CTA central counts stay below n < 2^32
   uint32_t* s_kmeta;
-  uint16_t* lut;              // bin lookup table (see QueryArgs)
-  uint32_t lut_shift, lut_base, lut_last;
+  uint32_t* lut;              // bin lookup table (see QueryArgs)
+  uint32_t lut_shift, lut_base, lut_mask;
   float Emax, E0, r0f, inv_dr;
   uint32_t nb;
 
   __device__ void init(const QueryArgs& a, unsigned char* smem, uint32_t stage_cap, bool allow_priv = false) {
     const SmemLayout L = smem_layout(a.n_bins, a.n_k, RDF, stage_cap, allow_priv, a.lut_n);
     sE = reinterpret_cast<float*>(smem + L.off_E);
-    lut = reinterpret_cast<uint16_t*>(smem + L.off_lut);
+    lut = reinterpret_cast<uint32_t*>(smem + L.off_lut);
     lut_shift = RDF ? a.lut_shift : 0u;
     lut_base = a.lut_base;
-    lut_last = a.lut_n ? a.lut_n - 1 : 0;
+    lut_mask = (1u << lut_shift) - 1u;
     priv = L.priv;
     s_rdf = reinterpret_cast<unsigned long long*>(smem + L.off_rdf);
     s_rdfw = reinterpret_cast<uint32_t*>(smem + L.off_rdf) + (threadIdx.x >> 5) * a.n_bins;
@@ -180,9 +180,12 @@ struct Hist {
     for (uint32_t b = threadIdx.x; b < 2 * a.n_k; b += blockDim.x) s_kmeta[b] = 0;
     __syncthreads();
     if (RDF && lut_shift) {
-      // entry c: the largest b < nb with E[b] <= the smallest value of cell c (0 below E[0])
+      // entry c = b0 << 17 | off: b0 the largest b < nb with E[b] <= the smallest value of cell c
+      // (0 below E[0]); off the low lut_shift bits of the next interior edge E[b0 + 1] if it lies
+      // in the cell (at most one does), else 2^16, above every low part
       for (uint32_t c = threadIdx.x; c < a.lut_n; c += blockDim.x) {
-        const float v = __uint_as_float((lut_base + c) << lut_shift);
+        const uint32_t c0 = (lut_base + c) << lut_shift;
+        const float v = __uint_as_float(c0);
         uint32_t lo = 0, hi = nb;  // invariant: E[lo] <= v or lo == 0; E[hi] > v or hi == nb
         while (hi - lo > 1) {
           const uint32_t mid = (lo + hi) >> 1;
@@ -191,7 +194,12 @@ struct Hist {
           else
             hi = mid;
         }
-        lut[c] = (uint16_t)lo;
+        uint32_t off = 1u << 16;
+        if (lo + 1 < nb) {
+          const uint32_t e = __float_as_uint(sE[lo + 1]);
+          if (e >= c0 && e - c0 <= lut_mask) off = e & lut_mask;
+        }
+        lut[c] = lo << 17 | off;
       }
       __syncthreads();
     }
@@ -204,12 +212,13 @@ struct Hist {
   // bin b in [0, nb) with E[b] <= d2 < E[b+1] for E[0] <= d2 < E[nb]: from the lookup table (the
   // cell of d2's bit pattern holds at most one interior edge, so the bin is the entry or the next
   // one), else from an approximate square root checked against the edges
+  // (d2 >= 0 below E[nb]; the table's first cell lies wholly below E[1], so values below the
+  // table take its entry, bin 0)
   __device__ __forceinline__ uint32_t bin(float d2) const {
     if (lut_shift) {
-      // below the first cell (whose start is at most E[1]) the bin is 0
-      const int32_t c = (int32_t)(__float_as_uint(d2) >> lut_shift) - (int32_t)lut_base;
-      const uint32_t b0 = c < 0 ? 0u : lut[(uint32_t)c > lut_last ? lut_last : (uint32_t)c];
-      return b0 + (d2 >= sE[b0 + 1] ? 1u : 0u);
+      const uint32_t u = __float_as_uint(d2);
+      const uint32_t e = lut[max((int32_t)(u >> lut_shift) - (int32_t)lut_base, 0)];
+      return (e >> 17) + ((u & lut_mask) >= (e & 0x1FFFFu) ? 1u : 0u);
     }
     return bin_index(d2, sE, nb, r0f, inv_dr);
   }
@@ -218,6 +227,10 @@ struct Hist {
   // binned are not counted here: the flushes add the rows' sums to the meta array.
   __device__ __forceinline__ void pair_w(float d2, uint32_t w, uint32_t& below) {
     if (!RDF) return;
+    if (E0 == 0.f && priv) {  // r0 = 0: every pair (d2 >= 0) is binned (uniform branch)
+      atomicAdd(&s_rdfw[bin(d2)], w);
+      return;
+    }
     const bool in = d2 >= E0;
     const uint32_t b = bin(in ? d2 : E0);
     if (priv)
@@ -896,14 +909,19 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   uint32_t* rpre = s_rpre[w];
   const float E_max = H.Emax;
 
-  // cells per take: 32, or fewer when the grid is small, so that every warp gets work (about four
-  // takes per warp)
+  // cells per take: a share of the cells left (at most 32, at least 1), so that the warps finish
+  // together -- a take of 32 cells is a large part of a warp's work on a small grid
   const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
-  const uint32_t take = min(32u, max(1u, (n_cells + 4 * n_warps - 1) / (4 * n_warps)));
   for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.cgeo->sym_next, take);
+    uint32_t base = 0, take = 0;
+    if (lane == 0) {
+      const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&a.cgeo->sym_next);
+      const uint32_t left = cur < n_cells ? n_cells - cur : 0u;
+      take = min(32u, max(1u, left / (8 * n_warps)));
+      base = atomicAdd(&a.cgeo->sym_next, take);
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
+    take = __shfl_sync(0xffffffffu, take, 0);
     if (base >= n_cells) break;
     uint32_t s0 = 0, s1 = 0;
     if (lane < take && base + lane < n_cells) s0 = a.nstart[base + lane], s1 = a.nstart[base + lane + 1];
@@ -990,7 +1008,7 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
           for (uint32_t k0 = 0; k0 < n_pr; k0 += 8) {
             const uint32_t k1 = min(n_pr, k0 + 8);
             uint32_t nh = 0;  // hits in the warp list (uniform)
-#pragma unroll 2
+#pragma unroll 4
             for (uint32_t k = k0; k < k1; ++k) {
               const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(gf)[2 * k];
               const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(gf)[2 * k + 1];
@@ -1077,31 +1095,32 @@ static int dispatch_k(const ps_grid* g, const QueryArgs& qa, uint32_t sc, uint32
   return launch_query<32, RDF>(g, qa, sc, sw, s);
 }
 
-// Parameters of the bin lookup table: the largest bit shift S at which the interior edges
+// Parameters of the bin lookup table: a bit shift S <= 16 at which the interior edges
 // E[1..nb-1] fall in strictly increasing cells of the float32 bit pattern (bits >> S), so that a
-// cell holds at most one edge; the table covers the cells from E[1]'s to E[nb]'s.  None when the
-// table would exceed kLutMax entries or two edges coincide.
+// cell holds at most one edge, whose low S bits its entry carries; the table covers the cells from
+// the one below E[1]'s to E[nb]'s.  The largest such S gives the smallest table.  None when the
+// table would exceed kLutMax entries, two edges coincide or nb >= 2^15.
 static void choose_lut(ps_bins bins, QueryArgs& qa) {
   qa.lut_shift = qa.lut_base = qa.lut_n = 0;
   const uint32_t nb = bins.n_bins;
-  if (nb < 2) return;
+  if (nb < 2 || nb >= (1u << 15)) return;
   std::vector<uint32_t> Eb(nb + 1);
   for (uint32_t b = 0; b <= nb; ++b) {
     const double e = bins.r0 + (double)b * bins.dr;
     const float f = (float)(e * e);
     memcpy(&Eb[b], &f, 4);
   }
-  for (int S = 30; S >= 1; --S) {
-    bool ok = true;
+  for (int S = 16; S >= 1; --S) {
+    bool ok = (Eb[1] >> S) >= 1;
     for (uint32_t b = 2; b < nb && ok; ++b) ok = (Eb[b] >> S) > (Eb[b - 1] >> S);
     if (!ok) continue;
-    const uint32_t base = Eb[1] >> S, n = (Eb[nb] >> S) - base + 1;
+    const uint32_t base = (Eb[1] >> S) - 1, n = (Eb[nb] >> S) - base + 1;
     if (n <= kLutMax) {
       qa.lut_shift = (uint32_t)S;
       qa.lut_base = base;
       qa.lut_n = n;
     }
-    return;  // the largest separating shift gives the smallest table
+    return;
   }
 }
 
