@@ -228,6 +228,61 @@ def candidate_tests(X, T, D, ctr, nbr, dsrf_min, info, stencil, chunk=1 << 26, a
     return tot
 
 
+def octant_tests(X, T, D, ctr, nbr, dsrf_min, info, chunk=1 << 26):
+    """Central x candidate tests of the near kNN pass on the 2 x 2 x 2 block of cells around the
+    central's nearest vertex: its cell and its neighbours on the side of its half along each axis
+    (the fraction of its float32 cell coordinate (x - origin) * inv_h at or above 1/2: the upper
+    neighbour), clipped at the grid's faces.  Counted like candidate_tests (reporting only; the
+    kernel's vertex cells use their own float32 origin, which can move a central lying within a
+    rounding error of a cell's midplane to the other block)."""
+    import torch
+
+    import paper_2004_05188_gb300 as ps
+
+    def lut(types):
+        m = ps.type_mask(types)
+        return torch.tensor([bool((int(m[t >> 6]) >> (t & 63)) & 1) for t in range(256)], device=T.device)
+
+    dims = info["dims"]
+    org = torch.tensor(info["origin"], dtype=torch.float32, device=X.device)
+    inv_h = torch.tensor(float(np.float32(1.0 / float(info["cell"]))), dtype=torch.float32, device=X.device)
+    ln, lc = lut(nbr), lut(ctr)
+    lim = torch.tensor(dims, dtype=torch.int64, device=X.device) - 1
+
+    def coords(P):
+        u = (P - org) * inv_h
+        c = torch.minimum(torch.floor(u).to(torch.int64).clamp_(min=0), lim)
+        return c, (u - c.to(torch.float32)) >= 0.5
+
+    n = X.shape[0]
+    cnt = torch.zeros(info["n_cells"], dtype=torch.int64, device=X.device)
+    for a in range(0, n, chunk):
+        sel = ln[T[a:a + chunk].long()]
+        c, _ = coords(X[a:a + chunk][sel])
+        cnt += torch.bincount((c[:, 2] * dims[1] + c[:, 1]) * dims[0] + c[:, 0], minlength=info["n_cells"])
+    cnt = cnt.view(dims[2], dims[1], dims[0])
+    tot = 0
+    for octant in range(8):
+        up = [(octant >> ax) & 1 for ax in range(3)]  # axis 0 = x (last tensor dim)
+        box = cnt
+        for ax in range(3):
+            dim = 2 - ax
+            pad = [0, 0] * (2 - dim) + ([0, 1] if up[ax] else [1, 0])
+            padded = torch.nn.functional.pad(box, pad)
+            sl = [slice(None)] * 3
+            sl[dim] = slice(1, None) if up[ax] else slice(0, -1)
+            box = box + padded[tuple(sl)]
+        box = box.reshape(-1)
+        for a in range(0, n, chunk):
+            cm = lc[T[a:a + chunk].long()] & (D[a:a + chunk] >= dsrf_min)
+            c, hi = coords(X[a:a + chunk][cm])
+            mine = (hi[:, 0] == bool(up[0])) & (hi[:, 1] == bool(up[1])) & (hi[:, 2] == bool(up[2]))
+            c = c[mine]
+            tot += int(box[(c[:, 2] * dims[1] + c[:, 1]) * dims[0] + c[:, 0]].sum().item())
+        del box
+    return tot
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -814,9 +869,10 @@ def rooflines(prof, st, steps, peaks, hbm_peak, hbm_src, traffic):
 def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil, split=False):
     """Counts of one combination after its build + query (reporting only, untimed).  candidates:
     the distance tests of the query -- one pass: every central against its stencil; in passes
-    (split): every central against its 27-cell stencil (near kNN) plus every unordered pair of
-    records in each other's stencil once (symmetric RDF), the few full-radius fallback searches
-    not counted."""
+    (split): every central against its near kNN block (its own 2 x 2 x 2 cells on half-size
+    cells, the 27 cells around its cell on third-size cells) plus every unordered pair of records
+    in each other's stencil once (symmetric RDF), the few full-radius fallback searches not
+    counted."""
     meta = o["meta"].cpu().numpy()
     if meta[3] != 0:
         raise RuntimeError(f"device status {meta[3]} for {name}")
@@ -827,7 +883,12 @@ def combo_stats(ps, g, o, name, ctr, nbr, X, T, D, t_host, wl, stencil, split=Fa
     subset = bool(np.all((mc & ~mn) == 0))
     cs = g.cell_scale
     if split and subset and stencil >= 2:
-        near = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, 1) if wl["ks"] else 0
+        if not wl["ks"]:
+            near = 0
+        elif stencil == 2:  # each central's own 2 x 2 x 2 block of cells
+            near = octant_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info)
+        else:  # the 27 cells around the central's cell
+            near = candidate_tests(X, T, D, ctr, nbr, wl["dsrf_min"], info, 1)
         full = candidate_tests(X, T, D, nbr, nbr, wl["dsrf_min"], info, stencil, all_records=True, cell_scale=cs)
         sym = (full - info["n_nbr"]) // 2
         by_pass = {"query": near, "rdf_sym": sym}

@@ -111,7 +111,7 @@ __global__ void k_reset(Geo* geo) {
     geo->status = 0;
     geo->work_n = geo->work_n2 = geo->work_n3 = geo->work_n4 = 0;
     geo->work_next = geo->work_next2 = geo->work_next3 = 0;
-    geo->work_next2b = geo->work_next3b = geo->sym_next = 0;
+    geo->work_next2b = geo->work_next3b = geo->sym_next = geo->list_n = 0;
   }
 }
 
@@ -217,13 +217,16 @@ __device__ void compute_geometry(const Geo& in, float r_cut, float cell_scale, u
   for (int a = 0; a < 3; ++a) ext = fmax(ext, hi[a] - lo[a]);
   double h = (double)r_cut * (double)cell_scale * (1.0 + 1.0 / 1024.0) + ext * (1.0 / 1048576.0);
   uint32_t dims[3] = {1, 1, 1};
+  // cells smaller than r_cut: room in the cell arrays for the grid of cells centred on the
+  // vertices (one more cell per axis) that the query in passes sorts its centrals by
+  const double extra = cell_scale < 1.0f ? 1.0 : 0.0;
   for (int it = 0; it < 256; ++it) {
     double tot = 1.0;
     for (int a = 0; a < 3; ++a) {
       double d = floor((hi[a] - lo[a]) / h) + 1.0;
       d = fmin(d, 2147483648.0);
       dims[a] = (uint32_t)d;
-      tot *= d;
+      tot *= d + extra;
     }
     if (tot <= (double)cell_cap) break;
     h *= 1.2599210498948732;  // 2^(1/3): halve the cell count
@@ -349,7 +352,7 @@ __global__ void k_central_reset(const Geo* __restrict__ ngeo, Geo* cgeo, uint32_
     cgeo->status = 0;
     cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = cgeo->work_n4 = 0;
     cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
-    cgeo->work_next2b = cgeo->work_next3b = cgeo->sym_next = 0;
+    cgeo->work_next2b = cgeo->work_next3b = cgeo->sym_next = cgeo->list_n = 0;
   }
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (uint32_t c = tid; c < nc; c += stride) count[c] = 0;
@@ -518,7 +521,8 @@ __device__ __forceinline__ void emit_items(const uint32_t (&v)[kScanItems], uint
     if (dense) work[s1] = c0 + k;
     const uint32_t cand = (!dense && v[k] > 0 && nstart != nullptr) ? stencil_count(nstart, geo, c0 + k, stencil) : 0u;
     sparse[k] = !dense && v[k] > 0 && v[k] < kHeavy && nstart != nullptr && cand <= kSparseCand;
-    lanes[k] = (split && !sparse[k] && v[k] > 3) ? lanes_per_central(cand, n_nbr, nc, stencil) : 1u;
+    lanes[k] = (split && nstart != nullptr && !sparse[k] && v[k] > 3) ? lanes_per_central(cand, n_nbr, nc, stencil)
+                                                                        : 1u;
     cands[k] = cand;
     if (!dense && sparse[k]) n_back += items_of(v[k], lanes[k]);
     if (!dense && !sparse[k]) {
@@ -618,23 +622,29 @@ __global__ void __launch_bounds__(kScanThreads) k_central_subset(const float4* _
                                                                  const float* __restrict__ dsrf, Mask mask,
                                                                  float dsrf_min, float4* __restrict__ crec,
                                                                  uint32_t* __restrict__ pfx, unsigned long long* state,
-                                                                 uint32_t* ctr, ZeroOut z) {
+                                                                 uint32_t* ctr, ZeroOut z, uint32_t* __restrict__ vcount) {
   griddep_wait();
   griddep_launch();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_tile, s_prefix;
   const uint32_t nr = ngeo->n_sel;
+  // vcount given: the central list is the grid of cells centred on the vertices (origin half a
+  // cell lower, one more cell per axis), filled by k_vertex_count / k_vertex_scatter; its counts
+  // are zeroed here and no records are written
+  const uint32_t nvc = (ngeo->dims[0] + 1) * (ngeo->dims[1] + 1) * (ngeo->dims[2] + 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // every field but n_sel, which the thread that scans the last tile writes
-    for (int a = 0; a < 3; ++a) cgeo->origin[a] = ngeo->origin[a], cgeo->dims[a] = ngeo->dims[a];
+    const float half = vcount ? __fmul_rn(0.5f, ngeo->h) : 0.0f;
+    for (int a = 0; a < 3; ++a)
+      cgeo->origin[a] = __fsub_rn(ngeo->origin[a], half), cgeo->dims[a] = ngeo->dims[a] + (vcount ? 1u : 0u);
     for (int a = 0; a < 6; ++a) cgeo->bbox_key[a] = ngeo->bbox_key[a];
     cgeo->inv_h = ngeo->inv_h;
     cgeo->h = ngeo->h;
-    cgeo->n_cells = ngeo->n_cells;
+    cgeo->n_cells = vcount ? nvc : ngeo->n_cells;
     cgeo->status = 0;
     cgeo->work_n = cgeo->work_n2 = cgeo->work_n3 = cgeo->work_n4 = 0;
     cgeo->work_next = cgeo->work_next2 = cgeo->work_next3 = 0;
-    cgeo->work_next2b = cgeo->work_next3b = cgeo->sym_next = 0;
+    cgeo->work_next2b = cgeo->work_next3b = cgeo->sym_next = cgeo->list_n = 0;
     if (nr == 0) pfx[0] = 0, cgeo->n_sel = 0;
   }
   {
@@ -642,6 +652,8 @@ __global__ void __launch_bounds__(kScanThreads) k_central_subset(const float4* _
     for (int k = 0; k < 3; ++k)
       if (z.p[k])
         for (uint32_t i = tid; i < z.n[k]; i += stride) z.p[k][i] = 0ull;
+    if (vcount)
+      for (uint32_t i = tid; i < nvc; i += stride) vcount[i] = 0u;
   }
   const uint32_t tiles = (nr + kScanTile - 1) / kScanTile;
   for (;;) {
@@ -677,7 +689,7 @@ __global__ void __launch_bounds__(kScanThreads) k_central_subset(const float4* _
     for (int k = 0; k < kScanItems; ++k) {
       if (j0 + k < nr) {
         pfx[j0 + k] = run;
-        if (f[k]) crec[run] = r[k];
+        if (f[k] && crec) crec[run] = r[k];
       }
       run += f[k];
     }
@@ -716,6 +728,46 @@ __global__ void __launch_bounds__(kThreads) k_central_items(const uint32_t* __re
       }
     }
     emit_items(v, c0, nc, cgeo, work, witem, dense_min, cap, nstart, stencil, split, whi);
+  }
+}
+
+// Central list on the vertex-centred grid (cgeo: origin half a cell below the neighbour grid's,
+// one more cell per axis), for the query in passes: the centrals of the cell around vertex V are
+// those nearest to V, and the 2 x 2 x 2 neighbour cells around V hold every record within half a
+// cell of each of them.  Counting sort of the flagged neighbour records (pfx), in the record
+// order: count + rank here, starts by k_scan, records by k_vertex_scatter.
+__global__ void __launch_bounds__(kThreads) k_vertex_count(const float4* __restrict__ nrec,
+                                                           const Geo* __restrict__ ngeo, const Geo* __restrict__ cgeo,
+                                                           const uint32_t* __restrict__ pfx,
+                                                           uint32_t* __restrict__ count, uint32_t* __restrict__ rank) {
+  griddep_wait();
+  griddep_launch();
+  const uint32_t nr = ngeo->n_sel;
+  const Geo g = *cgeo;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nr; j += gridDim.x * blockDim.x) {
+    const uint32_t c0 = pfx[j];
+    if (pfx[j + 1] == c0) continue;
+    const float4 p = nrec[j];
+    rank[c0] = atomicAdd(&count[cell_of(g, p.x, p.y, p.z)], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_vertex_scatter(const float4* __restrict__ nrec,
+                                                             const Geo* __restrict__ ngeo,
+                                                             const Geo* __restrict__ cgeo,
+                                                             const uint32_t* __restrict__ pfx,
+                                                             const uint32_t* __restrict__ start,
+                                                             const uint32_t* __restrict__ rank,
+                                                             float4* __restrict__ crec) {
+  griddep_wait();
+  griddep_launch();
+  const uint32_t nr = ngeo->n_sel;
+  const Geo g = *cgeo;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nr; j += gridDim.x * blockDim.x) {
+    const uint32_t c0 = pfx[j];
+    if (pfx[j + 1] == c0) continue;
+    const float4 p = nrec[j];
+    crec[start[cell_of(g, p.x, p.y, p.z)] + rank[c0]] = p;
   }
 }
 
@@ -802,16 +854,38 @@ int build_neighbour_grid(ps_grid* g, const uint64_t nbr_mask[4], float r_cut, cu
 }
 
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
-                       ZeroOut z, bool split) {
+                       ZeroOut z, bool split, bool vertex) {
   Mask m;
   bool subset = !g->pack_type;
   for (int w = 0; w < 4; ++w) m.w[w] = ctr_mask[w], subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
+  if (subset && vertex) {
+    // the central prefix over the neighbour records, then the centrals sorted by the
+    // vertex-centred grid (ranks in the dense-cell list, unused without dense cells)
+    uint32_t* pfx = reinterpret_cast<uint32_t*>(g->cr);
+    PS_LAUNCH(PS_KID_CENTRAL, s,
+              PS_CUDA(launch_pdl(k_central_subset, grid_blocks(g, 1), kScanThreads, 0, s, g->nbr.rec, g->nbr.geo,
+                                 g->ctr.geo, g->type, dsrf, m, dsrf_min, (float4*)nullptr, pfx, g->scan_state,
+                                 g->scan_ctr, z, g->ctr.count)));
+    PS_LAUNCH(PS_KID_CENTRAL, s,
+              PS_CUDA(launch_pdl(k_vertex_count, grid_blocks(g, 8), kThreads, 0, s, g->nbr.rec, g->nbr.geo, g->ctr.geo,
+                                 pfx, g->ctr.count, g->ctr.work)));
+    PS_LAUNCH(PS_KID_SCAN, s,
+              PS_CUDA(launch_pdl(k_scan, grid_blocks(g, 1), kScanThreads, 0, s, g->ctr.count, g->ctr.geo, g->ctr.start,
+                                 g->ctr.work, g->ctr.witem, 0xFFFFFFFFu, g->item_cap, g->scan_state, g->scan_ctr,
+                                 (const uint32_t*)nullptr, g->stencil, true, (uint2*)nullptr)));
+    PS_LAUNCH(PS_KID_SCATTER, s,
+              PS_CUDA(launch_pdl(k_vertex_scatter, grid_blocks(g, 8), kThreads, 0, s, g->nbr.rec, g->nbr.geo,
+                                 g->ctr.geo, pfx, g->ctr.start, g->ctr.work, g->ctr.rec)));
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+  }
   if (subset) {
     // centrals are neighbour records: compact the cell-sorted records (2 kernels)
     uint32_t* pfx = reinterpret_cast<uint32_t*>(g->cr);  // 2 n_max words, n_records + 1 needed
     PS_LAUNCH(PS_KID_CENTRAL, s,
               PS_CUDA(launch_pdl(k_central_subset, grid_blocks(g, 1), kScanThreads, 0, s, g->nbr.rec, g->nbr.geo,
-                                 g->ctr.geo, g->type, dsrf, m, dsrf_min, g->ctr.rec, pfx, g->scan_state, g->scan_ctr, z)));
+                                 g->ctr.geo, g->type, dsrf, m, dsrf_min, g->ctr.rec, pfx, g->scan_state, g->scan_ctr, z,
+                                 (uint32_t*)nullptr)));
     PS_LAUNCH(PS_KID_SCAN, s,
               PS_CUDA(launch_pdl(k_central_items, grid_blocks(g, 4), kThreads, 0, s, g->nbr.start, pfx, g->ctr.geo,
                                  g->ctr.start, g->ctr.work, g->ctr.witem, g->dense_min, g->item_cap, g->stencil, split,

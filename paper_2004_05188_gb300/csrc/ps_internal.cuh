@@ -84,6 +84,7 @@ struct Geo {
   uint32_t work_next2b;  // second pass over the same items (the exact query's full-radius kNN fallback)
   uint32_t work_next3b;
   uint32_t sym_next;     // cells taken by the symmetric RDF pass (32 at a time)
+  uint32_t list_n;       // centrals listed by the near kNN pass for the full-radius search
 };
 
 // Warp items with at least this many centrals per cell are listed first (largest work first).
@@ -208,9 +209,11 @@ struct ZeroOut {
   uint64_t* p[3] = {nullptr, nullptr, nullptr};
   uint32_t n[3] = {0, 0, 0};
 };
-// split: size the warp items of dense cells for lanes_per_central (the exact query's staged path)
+// split: size the warp items of dense cells for lanes_per_central (the exact query's staged path);
+// vertex: centrals among the neighbour records sorted by the vertex-centred grid (the query in
+// passes on cells smaller than r_cut), the central prefix in g->cr
 int build_central_list(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, cudaStream_t s,
-                       ZeroOut z = ZeroOut(), bool split = false);
+                       ZeroOut z = ZeroOut(), bool split = false, bool vertex = false);
 int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, float sigma, float scale,
                  ps_bins bins, float* d_h, cudaStream_t s);
 int run_sdm(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float dsrf_min, ps_sdm_spec spec,

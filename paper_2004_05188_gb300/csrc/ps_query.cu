@@ -65,6 +65,7 @@ struct QueryArgs {
   uint32_t* next_front;   // work counters of the front (heavy) and back (light) items
   uint32_t* next_light;
   const uint32_t* pfx;    // symmetric RDF pass: central prefix over the neighbour records
+  int vertex;             // near kNN pass on the vertex-centred central list (see vertex_run)
   // bin lookup table (lut_shift = 0: none): cell c covers the float32 bit patterns
   // [(lut_base + c) << lut_shift, (lut_base + c + 1) << lut_shift), at most one interior edge each
   uint32_t lut_shift, lut_base, lut_n;
@@ -381,6 +382,57 @@ __device__ __forceinline__ void cell_run(const QueryArgs& a, const Geo& ng, uint
   row_run(a, ng, cx, (int)cy + dy, (int)cz + dz, row_width(a, dy, dz), src, len);
 }
 
+// Near kNN pass of the query in passes (vertex != 0): the central list is sorted by the grid
+// of cells centred on the vertices of the neighbour grid (vg: origin half a cell lower, one more
+// cell per axis), so the centrals of item cell c are those nearest to vertex V = c's coordinates,
+// and the 2 x 2 x 2 neighbour cells V - 1 .. V along each axis hold every record within half a
+// cell of each of them: 4 rows of 2 cells, ~8 cells of candidates instead of the 27 around a
+// central's cell.  Run r < 4 of that block:
+__device__ __forceinline__ void vertex_run(const QueryArgs& a, const Geo& ng, const Geo& vg, uint32_t c, uint32_t r,
+                                           uint32_t& src, uint32_t& len) {
+  src = 0;
+  len = 0;
+  if (r >= 4) return;
+  const int vx = (int)(c % vg.dims[0]), vy = (int)((c / vg.dims[0]) % vg.dims[1]), vz = (int)(c / (vg.dims[0] * vg.dims[1]));
+  const int y = vy - 1 + (int)(r & 1u), z = vz - 1 + (int)(r >> 1);
+  const int xlo = max(vx - 1, 0), xhi = min(vx, (int)ng.dims[0] - 1);
+  if (y < 0 || z < 0 || y >= (int)ng.dims[1] || z >= (int)ng.dims[2] || xlo > xhi) return;
+  const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+  src = a.nstart[row + xlo];
+  len = a.nstart[row + xhi + 1] - src;
+}
+
+// The squared reach of central p in vertex cell c: the distance from p to the nearest face of
+// the block (cells V - 1 .. V + 1 in the neighbour grid's cell coordinate u = (x - origin) *
+// inv_h), less a slack for the float32 rounding of the cell coordinates of p and of any record
+// (a few ulps of u, below slack cells), times the cell edge, shrunk by 2^-12 before and after
+// squaring: every record outside the block has d2 above it, so a k-th distance below it is the
+// k-th distance over the whole cloud.  Capped at E[nb].
+__device__ __forceinline__ float vertex_reach(const Geo& ng, const Geo& vg, uint32_t c, const float4& p, float slack,
+                                              float h_eff, float Emax) {
+  const uint32_t v[3] = {c % vg.dims[0], (c / vg.dims[0]) % vg.dims[1], c / (vg.dims[0] * vg.dims[1])};
+  const float pc[3] = {p.x, p.y, p.z};
+  float m = INFINITY;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const float u = __fmul_rn(__fsub_rn(pc[ax], ng.origin[ax]), ng.inv_h);
+    m = fminf(m, fminf(__fsub_rn(u, (float)v[ax] - 1.0f), __fsub_rn((float)v[ax] + 1.0f, u)));
+  }
+  const float r = __fmul_rn(fmaxf(__fsub_rn(m, slack), 0.0f), h_eff);
+  return fminf(__fmul_rn(__fmul_rn(r, r), 1.0f - 1.0f / 4096.0f), Emax);
+}
+
+// Lists the centrals (positions in the central list) of the lanes with miss set, warp-aggregated
+// (all 32 lanes call it).
+__device__ __forceinline__ void list_append(const QueryArgs& a, bool miss, uint32_t pos, uint32_t lane) {
+  const uint32_t m = __ballot_sync(0xffffffffu, miss);
+  if (!m) return;
+  uint32_t at = 0;
+  if (lane == 0) at = atomicAdd(&a.cgeo->list_n, (uint32_t)__popc(m));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (miss) a.need[at + __popc(m & ((1u << lane) - 1u))] = pos;
+}
+
 __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(~0u)); }
 
 // ---------------------------------------------------------------------------
@@ -412,8 +464,13 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
   const Geo ng = *a.ngeo;
   const uint32_t n_hi = a.cgeo->work_n4, n_front = n_hi + a.cgeo->work_n2, n_light = a.cgeo->work_n3;
-  const int n_runs = (2 * a.stencil + 1) * (2 * a.stencil + 1);
+  const int n_runs = a.vertex ? 4 : (2 * a.stencil + 1) * (2 * a.stencil + 1);
   const float erange = a.emax_near > 0.f ? a.emax_near : H.Emax;  // squared search range of this pass
+  // vertex mode: the item cells are those of the vertex-centred grid (a.cgeo); rounding slack of
+  // a cell coordinate (cells) and the cell edge for vertex_reach
+  const Geo vg = *a.cgeo;
+  const float v_slack = (float)max(ng.dims[0], max(ng.dims[1], ng.dims[2])) * 5.0e-7f + 1.0e-6f;
+  const float v_heff = __fmul_rn(__fdiv_rn(1.0f, ng.inv_h), 1.0f - 1.0f / 4096.0f);
   uint64_t my_binned = 0;  // pairs counted straight into the global histogram
   uint32_t my_below = 0;   // pairs below E[0]
   float4* buf = s_buf[w];
@@ -432,8 +489,12 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.cstart[c] + first;
     // run table: sources and prefix counts of the candidate runs
-    const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre,
-                                      [&](uint32_t r, uint32_t& src, uint32_t& len) { cell_run(a, ng, c, r, src, len); });
+    const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre, [&](uint32_t r, uint32_t& src, uint32_t& len) {
+      if (a.vertex)
+        vertex_run(a, ng, vg, c, r, src, len);
+      else
+        cell_run(a, ng, c, r, src, len);
+    });
 
     // record at virtual candidate position pos (runs concatenated); rr is a run hint, nondecreasing in pos
     auto fetch = [&](uint32_t pos, int& rr) -> float4 {
@@ -461,7 +522,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) p = a.crec[c0 + ci];
       const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
-      const float emax = valid ? erange : -INFINITY;  // lanes without a central never hit
+      // lanes without a central never hit; vertex mode: each central's own reach
+      const float emax = valid ? (a.vertex ? vertex_reach(ng, vg, c, p, v_slack, v_heff, H.Emax) : erange) : -INFINITY;
       const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
       const uint32_t lt = (1u << lane) - 1u;
       float top[KK];
@@ -559,15 +621,21 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
         }
       }
+      bool miss = false;
       if (valid && sub == 0) {
         if (a.nwithin) a.nwithin[pidx] = within;
         if (KMAX > 0) {
-          const bool found = !(a.emax_near > 0.f) || topk_get(top, a.k_need - 1) < a.emax_near;
-          if (a.emax_near > 0.f) a.need[c0 + ci] = found ? 0u : 1u;
+          const float kd = topk_get(top, a.k_need - 1);
+          const bool found = a.vertex ? kd < emax : (!(a.emax_near > 0.f) || kd < a.emax_near);
+          if (a.vertex)
+            miss = !found;
+          else if (a.emax_near > 0.f)
+            a.need[c0 + ci] = found ? 0u : 1u;
           if (found)
             for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
         }
       }
+      if (a.vertex) list_append(a, miss, c0 + ci, lane);
     } else {
       // few centrals, many candidates: the lanes split the candidates of each central and
       // merge their sorted lists by shuffles
@@ -575,6 +643,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         if (a.fallback && a.need[c0 + ci] == 0u) continue;  // warp-uniform
         const float4 p = a.crec[c0 + ci];
         const uint32_t pidx = __float_as_uint(p.w);
+        const float er = a.vertex ? vertex_reach(ng, vg, c, p, v_slack, v_heff, H.Emax) : erange;
         float top[KK];
 #pragma unroll
         for (int t = 0; t < KK; ++t) top[t] = INFINITY;
@@ -583,7 +652,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         for (uint32_t b = 0; b < n_cand; b += 32) {
           const float4 q = fetch(b + lane, rr);
           const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-          if (d2 < erange && __float_as_uint(q.w) != pidx) {
+          if (d2 < er && __float_as_uint(q.w) != pidx) {
             ++within;
             H.pair(a, d2, my_below);
             if (KMAX > 0) topk_insert(top, d2);
@@ -614,8 +683,12 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
           __syncwarp();
           if (lane == 0) {
-            const bool found = !(a.emax_near > 0.f) || m < a.emax_near;
-            if (a.emax_near > 0.f) a.need[c0 + ci] = found ? 0u : 1u;
+            const bool found = a.vertex ? m < er : (!(a.emax_near > 0.f) || m < a.emax_near);
+            if (a.vertex) {
+              if (!found) a.need[atomicAdd(&a.cgeo->list_n, 1u)] = c0 + ci;
+            } else if (a.emax_near > 0.f) {
+              a.need[c0 + ci] = found ? 0u : 1u;
+            }
             if (found)
               for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, kq[a.ks[q] - 1], pidx);
           }
@@ -1048,6 +1121,90 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
   add_pair_counters(a, my_binned, my_below);
 }
 
+// ---------------------------------------------------------------------------
+// full-radius kNN of the centrals the near pass could not settle
+// ---------------------------------------------------------------------------
+// Full-radius kNN of the centrals listed by the near pass: one lane per listed central walks its
+// stencil row by row (nearest rows first, each row's x-run within its width), the k_need smallest
+// d2 below E[nb] kept through the per-lane queue; fewer than k of them: not found (INF).
+template <int KMAX>
+__global__ void __launch_bounds__(256) k_knn_list(const QueryArgs a) {
+  griddep_wait();
+  griddep_launch();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float s_kq[8][17 * 32];
+  Hist<false> H{};
+  H.init(a, smem, 0, true);
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* kq = s_kq[w];
+  const Geo ng = *a.ngeo;
+  const float Emax = H.Emax;
+  const uint32_t n_list = a.cgeo->list_n;
+  const int s = a.stencil, n_rows = (2 * s + 1) * (2 * s + 1);
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t base = (blockIdx.x * (blockDim.x >> 5) + w) * 32u; base < n_list; base += n_warps * 32u) {
+    const bool valid = base + lane < n_list;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t c = 0;
+    if (valid) {
+      p = a.crec[a.need[base + lane]];
+      c = cell_of(ng, p.x, p.y, p.z);
+    }
+    const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
+    float top[KMAX];
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) top[t] = INFINITY;
+    for (int r = 0; r < n_rows; ++r) {
+      uint32_t src = 0, len = 0;
+      if (valid) cell_run(a, ng, c, (uint32_t)r, src, len);
+      const uint32_t n_max = __reduce_max_sync(0xffffffffu, len);
+      for (uint32_t t0 = 0; t0 < n_max; t0 += 16) {
+        const float thr = fminf(top[KMAX - 1], Emax);  // in range only: fewer than k leaves INF
+        uint32_t qn = 0;
+#pragma unroll 4
+        for (uint32_t u = 0; u < 16; ++u) {
+          const uint32_t t = t0 + u;
+          float4 q = far_record();
+          if (t < len) q = __ldg(a.nrec + src + t);
+          const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+          kq[qn * 32 + lane] = d2;
+          qn += (d2 < thr && __float_as_uint(q.w) != pidx) ? 1u : 0u;
+        }
+        const uint32_t m = __reduce_max_sync(0xffffffffu, qn);
+        for (uint32_t q = 0; q < m; ++q)
+          if (q < qn) topk_insert(top, kq[q * 32 + lane]);
+        __syncwarp();
+      }
+    }
+    if (valid)
+      for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
+  }
+  H.flush(a);
+}
+
+template <int KMAX>
+static int launch_knn_list(const ps_grid* g, const QueryArgs& qa, uint32_t smem, cudaStream_t s) {
+  auto k = k_knn_list<KMAX>;
+  int per_sm = 0;
+  PS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
+  if (per_sm < 1) return fail(PS_ERR_UNSUPPORTED, "full-radius kNN kernel does not fit on an SM");
+  PS_LAUNCH(PS_KID_KNN_FULL, s, PS_CUDA(launch_pdl(k, g->num_sms * per_sm, 256, smem, s, qa)));
+  return PS_OK;
+}
+
+static int dispatch_knn_list(const ps_grid* g, const QueryArgs& qa, uint32_t smem, cudaStream_t s) {
+  const uint32_t k = qa.k_need;
+  if (k <= 1) return launch_knn_list<1>(g, qa, smem, s);
+  if (k <= 2) return launch_knn_list<2>(g, qa, smem, s);
+  if (k <= 4) return launch_knn_list<4>(g, qa, smem, s);
+  if (k <= 8) return launch_knn_list<8>(g, qa, smem, s);
+  if (k <= 10) return launch_knn_list<10>(g, qa, smem, s);
+  if (k <= 12) return launch_knn_list<12>(g, qa, smem, s);
+  if (k <= 16) return launch_knn_list<16>(g, qa, smem, s);
+  return launch_knn_list<32>(g, qa, smem, s);
+}
+
 // Writes n_central and the device status into the meta array.
 __global__ void k_query_epilogue(const Geo* __restrict__ ngeo, const Geo* __restrict__ cgeo, uint64_t* meta) {
   griddep_wait();
@@ -1186,7 +1343,13 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   if (rdf) z.p[1] = d_rdf, z.n[1] = bins.n_bins;
   if (n_k) z.p[2] = d_knn, z.n[2] = n_k * bins.n_bins;
 
-  int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z, true);
+  bool subset = !g->pack_type;
+  for (int w = 0; w < 4; ++w) subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
+  // the query in passes, and its near kNN pass on the vertex-centred central list (two-cell
+  // stencils; the ranks of that counting sort take one word per central of the cell arrays)
+  const bool split = g->split && subset && rdf && d_nwithin == nullptr && g->stencil >= 2 && g->dense_min == 0xFFFFFFFFu;
+  const bool vertex = split && n_k > 0 && g->stencil == 2 && (uint64_t)g->n <= (uint64_t)g->cell_cap;
+  int rc = build_central_list(g, dsrf, ctr_mask, dsrf_min, s, z, true, vertex);
   if (rc) return rc;
 
   // staging budget of the CTA kernel: two CTAs per SM
@@ -1200,30 +1363,40 @@ int run_query(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], float d
   qa.stage_cap = (stage_bytes / 16) & ~7u;
   const uint32_t smem_cta = smem_layout(bins.n_bins, n_k, rdf, qa.stage_cap, false, qa.lut_n).total;
   const uint32_t smem_warp = smem_layout(bins.n_bins, n_k, rdf, 0, true, qa.lut_n).total;
-  bool subset = !g->pack_type;
-  for (int w = 0; w < 4; ++w) subset = subset && (ctr_mask[w] & ~g->nbr_mask[w]) == 0;
-  if (g->split && subset && rdf && d_nwithin == nullptr && g->stencil >= 2 && g->dense_min == 0xFFFFFFFFu) {
-    // the query in passes: (1) kNN within the cell edge r_cut * cell_scale (27 cells of the
-    // grid), centrals with fewer than k_need neighbours there marked; (2) the full-radius kNN
-    // of the marked centrals; (3) the RDF over unordered pairs
+  if (split) {
+    // the query in passes: (1) kNN near each central, centrals with fewer than k_need
+    // neighbours there set apart; (2) their full-radius kNN; (3) the RDF over unordered pairs
     if (n_k > 0) {
       QueryArgs qn = qa;
-      const double rk = (double)g->r_cut * (double)g->cell_scale;
-      double e = bins.r0 + (double)bins.n_bins * bins.dr;
-      const float Emax = (float)(e * e), Ek = (float)(rk * rk);
-      qn.emax_near = Ek < Emax ? Ek : Emax;
-      qn.stencil = 1;
-      row_widths(1, 1.0, qn.row_w);
       qn.need = g->sel;  // free between a build and the next one (the counting sort's index list)
-      rc = dispatch_k<false>(g, qn, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
-      if (rc) return rc;
-      QueryArgs qf = qa;
-      qf.fallback = 1;
-      qf.need = g->sel;
-      qf.next_front = &g->ctr.geo->work_next2b;
-      qf.next_light = &g->ctr.geo->work_next3b;
-      rc = dispatch_k<false>(g, qf, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
-      if (rc) return rc;
+      const uint32_t smem_knn = smem_layout(bins.n_bins, n_k, false, 0, true).total;
+      if (vertex) {
+        // the 2 x 2 x 2 cells around each central's nearest vertex, each central within its own
+        // reach (k_query_warp, vertex mode); the others listed for k_knn_list
+        qn.vertex = 1;
+        rc = dispatch_k<false>(g, qn, smem_cta, smem_knn, s);
+        if (rc) return rc;
+        rc = dispatch_knn_list(g, qn, smem_knn, s);
+        if (rc) return rc;
+      } else {
+        // the 27 cells around each central's cell, within the cell edge
+        const double rk = (double)g->r_cut * (double)g->cell_scale;
+        double e = bins.r0 + (double)bins.n_bins * bins.dr;
+        const float Emax = (float)(e * e), Ek = (float)(rk * rk);
+        qn.emax_near = Ek < Emax ? Ek : Emax;
+        qn.stencil = 1;
+        row_widths(1, 1.0, qn.row_w);
+        rc = dispatch_k<false>(g, qn, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
+        if (rc) return rc;
+        // the full radius for the centrals it marked
+        QueryArgs qf = qa;
+        qf.fallback = 1;
+        qf.need = g->sel;
+        qf.next_front = &g->ctr.geo->work_next2b;
+        qf.next_light = &g->ctr.geo->work_next3b;
+        rc = dispatch_k<false>(g, qf, smem_cta, smem_layout(bins.n_bins, n_k, false, 0, true).total, s);
+        if (rc) return rc;
+      }
     }
     QueryArgs qs = qa;
     qs.n_k = 0;

@@ -148,6 +148,32 @@ def test_symmetric_pass_test_count_brute_force(stencil, h, cs):
     assert (full - n) // 2 == pairs and (full - n) % 2 == 0
 
 
+def test_octant_tests_brute_force():
+    """The near kNN pass tests every central against the records of its own 2 x 2 x 2 block:
+    its cell and the neighbour on the side of its half along each axis (clipped at the faces)."""
+    rng = np.random.default_rng(9)
+    n = 3000
+    xyz = (rng.random((n, 3)) * np.array([7.0, 5.0, 9.0])).astype(np.float32)
+    t = rng.integers(0, 3, n).astype(np.uint8)
+    d = (rng.random(n) * 3.0).astype(np.float32)
+    h = 1.0
+    org = xyz.min(axis=0)
+    dims = tuple(int(np.floor((xyz[:, a].max() - org[a]) / h)) + 1 for a in range(3))
+    info = dict(dims=dims, origin=tuple(float(v) for v in org), cell=h, n_cells=dims[0] * dims[1] * dims[2])
+    got = bench.octant_tests(torch.from_numpy(xyz), torch.from_numpy(t), torch.from_numpy(d), [1], [0, 1], 1.0, info)
+    inv_h = np.float32(1.0 / h)
+    cn = _cells_np(xyz[np.isin(t, [0, 1])], org, inv_h, dims)
+    P = xyz[(t == 1) & (d >= 1.0)]
+    u = (P - org.astype(np.float32)).astype(np.float32) * inv_h
+    cc = np.clip(np.floor(u).astype(np.int64), 0, np.array(dims) - 1)
+    side = np.where(u - cc.astype(np.float32) >= 0.5, 1, -1)
+    want = 0
+    for c, sg in zip(cc, side):
+        lo, hi = np.minimum(c, c + sg), np.maximum(c, c + sg)
+        want += int(np.all((cn >= lo) & (cn <= hi), axis=1).sum())
+    assert got == want > 0
+
+
 def test_row_widths_rule():
     """Half-size cells keep every cell of the 5 x 5 x 5 stencil; third-size cells drop the 4 far
     corner cells of each octant (32 of 343); cells of 0.75 r_cut drop the rows (+-2, +-2) and the
