@@ -1124,9 +1124,13 @@ __global__ void __launch_bounds__(256, 4) k_rdf_sym(const QueryArgs a) {
 // ---------------------------------------------------------------------------
 // full-radius kNN of the centrals the near pass could not settle
 // ---------------------------------------------------------------------------
-// Full-radius kNN of the centrals listed by the near pass: one lane per listed central walks its
-// stencil row by row (nearest rows first, each row's x-run within its width), the k_need smallest
-// d2 below E[nb] kept through the per-lane queue; fewer than k of them: not found (INF).
+// Full-radius kNN of the centrals listed by the near pass: one lane per listed central, in two
+// tiers: (A) the 27 cells around its cell (every record within one cell of it; the central's
+// reach is its distance to the faces of that block, less the rounding slack), then, for the
+// warps with a central whose k-th distance is not within that reach, (B) the rest of its stencil
+// (the outer cells of the 9 inner rows and the outer rows).  Each tier walks its rows (nearest
+// first) with the k_need smallest d2 below E[nb] kept through the per-lane queue; fewer than k of
+// them: not found (INF).
 template <int KMAX>
 __global__ void __launch_bounds__(256) k_knn_list(const QueryArgs a) {
   griddep_wait();
@@ -1141,22 +1145,42 @@ __global__ void __launch_bounds__(256) k_knn_list(const QueryArgs a) {
   const float Emax = H.Emax;
   const uint32_t n_list = a.cgeo->list_n;
   const int s = a.stencil, n_rows = (2 * s + 1) * (2 * s + 1);
+  const float slack = (float)max(ng.dims[0], max(ng.dims[1], ng.dims[2])) * 5.0e-7f + 1.0e-6f;
+  const float h_eff = __fmul_rn(__fdiv_rn(1.0f, ng.inv_h), 1.0f - 1.0f / 4096.0f);
   const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t base = (blockIdx.x * (blockDim.x >> 5) + w) * 32u; base < n_list; base += n_warps * 32u) {
     const bool valid = base + lane < n_list;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t c = 0;
+    int cc[3] = {0, 0, 0};
+    float reach = -1.0f;
     if (valid) {
       p = a.crec[a.need[base + lane]];
-      c = cell_of(ng, p.x, p.y, p.z);
+      const float pc[3] = {p.x, p.y, p.z};
+      float m = INFINITY;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const float u = __fmul_rn(__fsub_rn(pc[ax], ng.origin[ax]), ng.inv_h);
+        int c = __float2int_rd(u);
+        c = c < 0 ? 0 : (c >= (int)ng.dims[ax] ? (int)ng.dims[ax] - 1 : c);
+        cc[ax] = c;
+        m = fminf(m, fminf(__fsub_rn(u, (float)c - 1.0f), __fsub_rn((float)c + 2.0f, u)));
+      }
+      const float r = __fmul_rn(fmaxf(__fsub_rn(m, slack), 0.0f), h_eff);
+      reach = fminf(__fmul_rn(__fmul_rn(r, r), 1.0f - 1.0f / 4096.0f), Emax);
     }
     const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
     float top[KMAX];
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) top[t] = INFINITY;
-    for (int r = 0; r < n_rows; ++r) {
+    // one x-run per lane: the records of cells xlo..xhi of row (y, z), for the lanes in `act`
+    auto walk = [&](bool act, int y, int z, int xlo, int xhi) {
       uint32_t src = 0, len = 0;
-      if (valid) cell_run(a, ng, c, (uint32_t)r, src, len);
+      xlo = max(xlo, 0), xhi = min(xhi, (int)ng.dims[0] - 1);
+      if (act && xlo <= xhi && y >= 0 && z >= 0 && y < (int)ng.dims[1] && z < (int)ng.dims[2]) {
+        const uint32_t row = ((uint32_t)z * ng.dims[1] + (uint32_t)y) * ng.dims[0];
+        src = a.nstart[row + xlo];
+        len = a.nstart[row + xhi + 1] - src;
+      }
       const uint32_t n_max = __reduce_max_sync(0xffffffffu, len);
       for (uint32_t t0 = 0; t0 < n_max; t0 += 16) {
         const float thr = fminf(top[KMAX - 1], Emax);  // in range only: fewer than k leaves INF
@@ -1174,6 +1198,22 @@ __global__ void __launch_bounds__(256) k_knn_list(const QueryArgs a) {
         for (uint32_t q = 0; q < m; ++q)
           if (q < qn) topk_insert(top, kq[q * 32 + lane]);
         __syncwarp();
+      }
+    };
+    // tier A: the 9 inner rows over cx - 1 .. cx + 1 (the first 9 rows of the nearest-first order)
+    for (int r = 0; r < 9; ++r)
+      walk(valid, cc[1] + c_row_dy[r], cc[2] + c_row_dz[r], cc[0] - 1, cc[0] + 1);
+    const bool more = valid && !(topk_get(top, a.k_need - 1) < reach);
+    if (__ballot_sync(0xffffffffu, more)) {
+      // tier B: the outer cells of the inner rows, then the outer rows, each within its width
+      for (int r = 0; r < 9; ++r) {
+        const int dy = c_row_dy[r], dz = c_row_dz[r], wd = valid ? row_width(a, dy, dz) : -1;
+        walk(more && wd >= 2, cc[1] + dy, cc[2] + dz, cc[0] - wd, cc[0] - 2);
+        walk(more && wd >= 2, cc[1] + dy, cc[2] + dz, cc[0] + 2, cc[0] + wd);
+      }
+      for (int r = 9; r < n_rows; ++r) {
+        const int dy = c_row_dy[r], dz = c_row_dz[r], wd = valid ? row_width(a, dy, dz) : -1;
+        walk(more && wd >= 0, cc[1] + dy, cc[2] + dz, cc[0] - wd, cc[0] + wd);
       }
     }
     if (valid)
