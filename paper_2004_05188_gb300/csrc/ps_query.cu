@@ -448,7 +448,9 @@ __device__ __forceinline__ float4 far_record() { return make_float4(INFINITY, IN
 constexpr uint32_t kHalf = 16;                 // candidates per staging half-batch
 constexpr uint32_t kRowLaneCap = 1u << 25;     // per-central increments of the 32-bit warp row, then global
 
-template <int KMAX, bool RDF>
+// VX: the near kNN pass on the vertex-centred central list (a.vertex; kNN only), compiled apart
+// so that the other forms carry none of its code
+template <int KMAX, bool RDF, bool VX = false>
 __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   griddep_wait();
   griddep_launch();
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
   uint64_t wcount = 0;  // increments of this warp's private row since its last flush (uniform)
   const Geo ng = *a.ngeo;
   const uint32_t n_hi = a.cgeo->work_n4, n_front = n_hi + a.cgeo->work_n2, n_light = a.cgeo->work_n3;
-  const int n_runs = a.vertex ? 4 : (2 * a.stencil + 1) * (2 * a.stencil + 1);
+  const int n_runs = VX ? 4 : (2 * a.stencil + 1) * (2 * a.stencil + 1);
   const float erange = a.emax_near > 0.f ? a.emax_near : H.Emax;  // squared search range of this pass
   // vertex mode: the item cells are those of the vertex-centred grid (a.cgeo); rounding slack of
   // a cell coordinate (cells) and the cell edge for vertex_reach
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
     const uint32_t c0 = a.cstart[c] + first;
     // run table: sources and prefix counts of the candidate runs
     const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre, [&](uint32_t r, uint32_t& src, uint32_t& len) {
-      if (a.vertex)
+      if (VX)
         vertex_run(a, ng, vg, c, r, src, len);
       else
         cell_run(a, ng, c, r, src, len);
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
       if (valid) p = a.crec[c0 + ci];
       const uint32_t pidx = valid ? __float_as_uint(p.w) : ~0u;
       // lanes without a central never hit; vertex mode: each central's own reach
-      const float emax = valid ? (a.vertex ? vertex_reach(ng, vg, c, p, v_slack, v_heff, H.Emax) : erange) : -INFINITY;
+      const float emax = valid ? (VX ? vertex_reach(ng, vg, c, p, v_slack, v_heff, H.Emax) : erange) : -INFINITY;
       const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
       const uint32_t lt = (1u << lane) - 1u;
       float top[KK];
@@ -626,8 +628,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         if (a.nwithin) a.nwithin[pidx] = within;
         if (KMAX > 0) {
           const float kd = topk_get(top, a.k_need - 1);
-          const bool found = a.vertex ? kd < emax : (!(a.emax_near > 0.f) || kd < a.emax_near);
-          if (a.vertex)
+          const bool found = VX ? kd < emax : (!(a.emax_near > 0.f) || kd < a.emax_near);
+          if (VX)
             miss = !found;
           else if (a.emax_near > 0.f)
             a.need[c0 + ci] = found ? 0u : 1u;
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
             for (uint32_t q = 0; q < a.n_k; ++q) H.kth(a, q, topk_get(top, a.ks[q] - 1), pidx);
         }
       }
-      if (a.vertex) list_append(a, miss, c0 + ci, lane);
+      if (VX) list_append(a, miss, c0 + ci, lane);
     } else {
       // few centrals, many candidates: the lanes split the candidates of each central and
       // merge their sorted lists by shuffles
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
         if (a.fallback && a.need[c0 + ci] == 0u) continue;  // warp-uniform
         const float4 p = a.crec[c0 + ci];
         const uint32_t pidx = __float_as_uint(p.w);
-        const float er = a.vertex ? vertex_reach(ng, vg, c, p, v_slack, v_heff, H.Emax) : erange;
+        const float er = VX ? vertex_reach(ng, vg, c, p, v_slack, v_heff, H.Emax) : erange;
         float top[KK];
 #pragma unroll
         for (int t = 0; t < KK; ++t) top[t] = INFINITY;
@@ -683,8 +685,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           }
           __syncwarp();
           if (lane == 0) {
-            const bool found = a.vertex ? m < er : (!(a.emax_near > 0.f) || m < a.emax_near);
-            if (a.vertex) {
+            const bool found = VX ? m < er : (!(a.emax_near > 0.f) || m < a.emax_near);
+            if (VX) {
               if (!found) a.need[atomicAdd(&a.cgeo->list_n, 1u)] = c0 + ci;
             } else if (a.emax_near > 0.f) {
               a.need[c0 + ci] = found ? 0u : 1u;
@@ -1260,7 +1262,7 @@ __global__ void k_query_epilogue(const Geo* __restrict__ ngeo, const Geo* __rest
 template <int KMAX, bool RDF>
 static int launch_query(const ps_grid* g, const QueryArgs& qa, uint32_t smem_cta, uint32_t smem_warp, cudaStream_t s) {
   const uint32_t kid = qa.fallback ? PS_KID_KNN_FULL : PS_KID_QUERY;
-  auto kw = k_query_warp<KMAX, RDF>;
+  auto kw = (!RDF && qa.vertex) ? k_query_warp<KMAX, RDF, !RDF> : k_query_warp<KMAX, RDF>;
   PS_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_warp));
   int per_sm_w = 0;
   PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, kw, 256, smem_warp));
