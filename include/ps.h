@@ -107,10 +107,12 @@ typedef struct {
                          neighbour cells in shared memory with bulk copies; 0 = never */
   uint32_t split;     /* 1: with cell_scale < 1, an exact query that wants the RDF and no per-central
                          in-range counts, and central types among the neighbour types, runs in passes:
-                         kNN within the cell edge (27 cells) with a full-radius search only for the
-                         centrals that have fewer than k neighbours there, and the RDF over unordered
-                         pairs (each pair tested once, counted once per central end).  Same results;
-                         0 (default): one combined pass */
+                         kNN near each central (cell_scale >= 0.5: the 2 x 2 x 2 cells around its
+                         nearest grid vertex, within its distance to their faces; below 0.5: the 27
+                         cells around its cell) with a full-radius search only for the centrals that
+                         have fewer than k neighbours there, and the RDF over unordered pairs (each
+                         pair tested once, counted once per central end).  Same results; 0
+                         (default): one combined pass */
 } ps_grid_opts;
 
 typedef struct ps_grid ps_grid; /* opaque; owns its device scratch */
