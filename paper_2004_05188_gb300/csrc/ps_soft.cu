@@ -24,9 +24,11 @@
 // central) writes and pass B (one lane per neighbour, candidates = centrals)
 // adds.  Each gradient has one owner: no atomics on the gradient.  dL/ds sums
 // W d over the pairs with a central owner.
-// Both kernels test the candidates two at a time with packed float32; the
-// forward compacts the in-range pairs of every 16 candidates into a warp list
-// that all lanes bin; the adjoint runs the pair code under a branch per
+// Both kernels test the candidates two at a time with packed float32.  The
+// forward over unordered pairs takes the neighbour cells one by one: the half
+// stencil's records are the lanes and the cell's records are read from shared
+// memory by every lane at once; the in-range pairs are compacted into a warp
+// list that all lanes bin.  The adjoint runs the pair code under a branch per
 // candidate (its per-pair work needs the owner's accumulators).
 #include <cmath>
 #include <cstring>
@@ -110,24 +112,20 @@ __device__ __forceinline__ void soft_half_run(const SoftArgs& a, const Geo& ng, 
   len = a.nstart[row + xhi + 1] - src;
 }
 
-// Iterates the items of the owner list with the candidates staged 32 at a time as interleaved
-// pairs (xa xb ya yb za zb wa wb) and tested two at a time with packed float32 math; the
-// in-range pairs of every half-batch of 16 candidates go to a warp list that all lanes then
-// process: hit(d2, weight) for each.  item_hook(cnt, n_cand) runs once per item.
-// SYM (centrals among the neighbour records): owners are the neighbour records, each pair is met
-// once (the half stencil and the later records of the owner's cell) and weighs c_i + c_j, the
-// central flags of its ends from the central prefix; the staged .w is rc^2 for a central
-// candidate and -1 otherwise, the range max(owner's, candidate's), and the sign bit of a listed
-// d2 marks weight 2.  Otherwise owners are the centrals, candidates their full stencil of
-// neighbours, .w the ion index (the owner itself is skipped), weight 1.
-template <bool SYM, class H, class I>
+// Iterates the items of the owner list (the centrals; candidates: their full stencil of
+// neighbours, whose staged .w is the ion index so that the owner itself is skipped) with the
+// candidates staged 32 at a time as interleaved pairs (xa xb ya yb za zb wa wb) and tested two at
+// a time with packed float32 math; the in-range pairs of every half-batch of 16 candidates go to
+// a warp list that all lanes then process: hit(d2, 1) for each.  item_hook(cnt, n_cand) runs once
+// per item.
+template <class H, class I>
 __device__ __forceinline__ void soft_items_listed(const SoftArgs& a, float* bf, uint32_t* rsrc, uint32_t* rpre,
                                                   float* wlist, H&& hit, I&& item_hook) {
   const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
   const Geo ng = *a.ngeo;
   const uint32_t n_front = a.ogeo->work_n2, n_items = n_front + a.ogeo->work_n3;
   const int s = a.stencil, wd = 2 * s + 1;
-  const int n_runs = SYM ? s * wd + s + 1 : wd * wd;
+  const int n_runs = wd * wd;
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(&a.ogeo->work_next2, 1u);
@@ -137,47 +135,24 @@ __device__ __forceinline__ void soft_items_listed(const SoftArgs& a, float* bf, 
     const uint32_t c = it.x, first = it.y >> 6, cnt = it.y & 63u;
     const uint32_t c0 = a.ostart[c] + first;
     const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre, [&](uint32_t r, uint32_t& src, uint32_t& len) {
-      if (SYM)
-        soft_half_run(a, ng, c, r, src, len);
-      else
-        soft_run(a, ng, c, r, src, len);
+      soft_run(a, ng, c, r, src, len);
     });
-    const uint32_t a1 = SYM ? a.ostart[c + 1] : 0u;  // end of the owner's cell
-    item_hook(cnt, n_cand + (SYM ? a1 - c0 : 0u));
+    item_hook(cnt, n_cand);
     const bool valid = lane < cnt;
     float4 p = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-    float elane = -INFINITY;
-    uint32_t pidx = ~0u, w2lane = 0u;
+    float emax = -INFINITY;
+    uint32_t pidx = ~0u;
     if (valid) {
       p = a.orec[c0 + lane];
-      if (SYM) {
-        const bool cen = __ldg(a.pfx + c0 + lane + 1) > __ldg(a.pfx + c0 + lane);
-        elane = cen ? a.rc2u : -1.f;
-        w2lane = cen ? 0x80000000u : 0u;
-      } else {
-        pidx = __float_as_uint(p.w);
-        elane = a.rc2u;
-      }
-    }
-    if (SYM && valid) {
-      // pairs inside the owner's cell, j > i, each lane on its own (a small share of the pairs)
-      const float ci = w2lane ? 1.f : 0.f;
-      for (uint32_t j = c0 + lane + 1; j < a1; ++j) {
-        const float4 q = __ldg(a.nrec + j);
-        const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
-        const float wt = ci + (float)(__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
-        if (d2 < a.rc2u && wt > 0.f) hit(d2, wt);
-      }
+      pidx = __float_as_uint(p.w);
+      emax = a.rc2u;
     }
     const unsigned long long px = f2_pack(p.x, p.x), py = f2_pack(p.y, p.y), pz = f2_pack(p.z, p.z);
     int rr = 0;
     auto fetch = [&](uint32_t pos) -> float4 {
-      if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, SYM ? -1.f : __uint_as_float(~0u));
+      if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(~0u));
       while (pos >= rpre[rr + 1]) ++rr;
-      const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
-      float4 q = __ldg(a.nrec + j);
-      if (SYM) q.w = __ldg(a.pfx + j + 1) > __ldg(a.pfx + j) ? a.rc2u : -1.f;
-      return q;
+      return __ldg(a.nrec + rsrc[rr] + (pos - rpre[rr]));
     };
     float4 nxt = fetch(lane);
     for (uint32_t b = 0; b < n_cand; b += 32) {
@@ -199,29 +174,140 @@ __device__ __forceinline__ void soft_items_listed(const SoftArgs& a, float* bf, 
           float d2a, d2b, wa, wb;
           dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
           f2_unpack(zw.y, wa, wb);
-          bool ha, hb;
-          uint32_t va, vb;
-          if (SYM) {
-            ha = d2a < fmaxf(elane, wa), hb = d2b < fmaxf(elane, wb);
-            va = __float_as_uint(d2a) | (~__float_as_uint(wa) & w2lane);
-            vb = __float_as_uint(d2b) | (~__float_as_uint(wb) & w2lane);
-          } else {
-            ha = d2a < elane && __float_as_uint(wa) != pidx, hb = d2b < elane && __float_as_uint(wb) != pidx;
-            va = __float_as_uint(d2a), vb = __float_as_uint(d2b);
-          }
+          const bool ha = d2a < emax && __float_as_uint(wa) != pidx;
+          const bool hb = d2b < emax && __float_as_uint(wb) != pidx;
           const uint32_t ba = __ballot_sync(0xffffffffu, ha);
-          reinterpret_cast<uint32_t*>(wlist)[ha ? nh + __popc(ba & lt) : 512 + lane] = va;
+          wlist[ha ? nh + __popc(ba & lt) : 512 + lane] = d2a;
           nh += __popc(ba);
           const uint32_t bb = __ballot_sync(0xffffffffu, hb);
-          reinterpret_cast<uint32_t*>(wlist)[hb ? nh + __popc(bb & lt) : 512 + lane] = vb;
+          wlist[hb ? nh + __popc(bb & lt) : 512 + lane] = d2b;
           nh += __popc(bb);
         }
         __syncwarp();
-        for (uint32_t h = lane; h < nh; h += 32) {
-          const uint32_t v = reinterpret_cast<const uint32_t*>(wlist)[h];
-          hit(__uint_as_float(v & 0x7FFFFFFFu), (v >> 31) ? 2.f : 1.f);
+        for (uint32_t h = lane; h < nh; h += 32) hit(wlist[h], 1.f);
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// The forward over unordered pairs, cell by cell: a warp takes a share of the cells left (at
+// most 32, at least 1, from the counter a.ogeo->work_next2) and, for each non-empty cell, tests
+// the half stencil's records (the lanes, 32 per load, each in registers) against the cell's
+// records (staged in shared memory up to 64 at a time as interleaved pairs xa xb ya yb za zb ea
+// eb and read by every lane at once, two per packed test), so that the lanes stay busy whatever
+// the cell's record count; the pairs inside the cell (j > i) are tested by each lane on its own.
+// A record's e (and a candidate's) is rc^2 for a central and -1 otherwise: a pair is in range
+// below max(e_rec, e_cand), weight 2 (the sign bit of its listed d2) when both are central.
+// hit(d2, weight) per in-range pair; cell_hook(m, n_cand) once per cell before its pairs.
+template <class H, class C>
+__device__ __forceinline__ void soft_cells_sym(const SoftArgs& a, float* gf, uint32_t* rsrc, uint32_t* rpre,
+                                               uint32_t* wlist, H&& hit, C&& cell_hook) {
+  const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+  const Geo ng = *a.ngeo;
+  const uint32_t n_cells = ng.n_cells;
+  const int s = a.stencil, n_runs = s * (2 * s + 1) + s + 1;
+  const float E = a.rc2u;
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  for (;;) {
+    uint32_t base = 0, take = 0;
+    if (lane == 0) {
+      const uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&a.ogeo->work_next2);
+      const uint32_t left = cur < n_cells ? n_cells - cur : 0u;
+      take = min(32u, max(1u, left / (8 * n_warps)));
+      base = atomicAdd(&a.ogeo->work_next2, take);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    take = __shfl_sync(0xffffffffu, take, 0);
+    if (base >= n_cells) break;
+    uint32_t s0 = 0, s1 = 0;
+    if (lane < take && base + lane < n_cells) s0 = a.ostart[base + lane], s1 = a.ostart[base + lane + 1];
+    uint32_t todo = __ballot_sync(0xffffffffu, s1 > s0);
+    while (todo) {
+      const int src_lane = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const uint32_t c = base + (uint32_t)src_lane;
+      const uint32_t a0 = __shfl_sync(0xffffffffu, s0, src_lane), a1 = __shfl_sync(0xffffffffu, s1, src_lane);
+      const uint32_t n_cand = run_table(lane, n_runs, rsrc, rpre, [&](uint32_t r, uint32_t& src, uint32_t& len) {
+        soft_half_run(a, ng, c, r, src, len);
+      });
+      cell_hook(a1 - a0, n_cand + (a1 - a0));
+      // pairs inside the cell
+      for (uint32_t i0 = a0; i0 < a1; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        if (i < a1) {
+          const float4 p = __ldg(a.orec + i);
+          const float ci = (float)(__ldg(a.pfx + i + 1) - __ldg(a.pfx + i));
+          for (uint32_t j = i + 1; j < a1; ++j) {
+            const float4 q = __ldg(a.orec + j);
+            const float d2 = dist2(p.x, p.y, p.z, q.x, q.y, q.z);
+            const float wt = ci + (float)(__ldg(a.pfx + j + 1) - __ldg(a.pfx + j));
+            if (d2 < E && wt > 0.f) hit(d2, wt);
+          }
+        }
+      }
+      if (n_cand == 0) continue;
+      for (uint32_t g0 = a0; g0 < a1; g0 += 64) {
+        const uint32_t m = min(64u, a1 - g0), n_pr = (m + 1) >> 1;
+        __syncwarp();
+#pragma unroll
+        for (uint32_t h = 0; h < 64; h += 32) {
+          const uint32_t r = h + lane;
+          if (r < 2 * n_pr) {
+            float4 q = make_float4(INFINITY, INFINITY, INFINITY, -1.f);  // the pad of an odd group never hits
+            if (r < m) {
+              q = __ldg(a.orec + g0 + r);
+              q.w = __ldg(a.pfx + g0 + r + 1) > __ldg(a.pfx + g0 + r) ? E : -1.f;
+            }
+            float* d = gf + (r >> 1) * 8 + (r & 1);
+            d[0] = q.x, d[2] = q.y, d[4] = q.z, d[6] = q.w;
+          }
         }
         __syncwarp();
+        int rr = 0;
+        auto fetch = [&](uint32_t pos) -> float4 {
+          if (pos >= n_cand) return make_float4(INFINITY, INFINITY, INFINITY, -1.f);
+          while (pos >= rpre[rr + 1]) ++rr;
+          const uint32_t j = rsrc[rr] + (pos - rpre[rr]);
+          float4 q = __ldg(a.nrec + j);
+          q.w = __ldg(a.pfx + j + 1) > __ldg(a.pfx + j) ? E : -1.f;
+          return q;
+        };
+        float4 nxt = fetch(lane);
+        for (uint32_t b = 0; b < n_cand; b += 32) {
+          const float4 q = nxt;
+          nxt = fetch(b + 32 + lane);
+          const unsigned long long qx = f2_pack(q.x, q.x), qy = f2_pack(q.y, q.y), qz = f2_pack(q.z, q.z);
+          const float eq = q.w;
+          const uint32_t w2q = eq > 0.f ? 0x80000000u : 0u;
+          for (uint32_t k0 = 0; k0 < n_pr; k0 += 8) {
+            const uint32_t k1 = min(n_pr, k0 + 8);
+            uint32_t nh = 0;
+#pragma unroll 4
+            for (uint32_t k = k0; k < k1; ++k) {
+              const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(gf)[2 * k];
+              const ulonglong2 zw = reinterpret_cast<const ulonglong2*>(gf)[2 * k + 1];
+              float d2a, d2b, ea, eb;
+              dist2_x2(xy.x, xy.y, zw.x, qx, qy, qz, d2a, d2b);
+              f2_unpack(zw.y, ea, eb);
+              const bool ha = d2a < fmaxf(eq, ea), hb = d2b < fmaxf(eq, eb);
+              const uint32_t va = __float_as_uint(d2a) | (~__float_as_uint(ea) & w2q);
+              const uint32_t vb = __float_as_uint(d2b) | (~__float_as_uint(eb) & w2q);
+              const uint32_t ba = __ballot_sync(0xffffffffu, ha);
+              wlist[ha ? nh + __popc(ba & lt) : 512 + lane] = va;
+              nh += __popc(ba);
+              const uint32_t bb = __ballot_sync(0xffffffffu, hb);
+              wlist[hb ? nh + __popc(bb & lt) : 512 + lane] = vb;
+              nh += __popc(bb);
+            }
+            __syncwarp();
+            for (uint32_t h = lane; h < nh; h += 32) {
+              const uint32_t v = wlist[h];
+              hit(__uint_as_float(v & 0x7FFFFFFFu), (v >> 31) ? 2.f : 1.f);
+            }
+            __syncwarp();
+          }
+        }
       }
     }
   }
@@ -313,7 +399,7 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
   griddep_wait();
   griddep_launch();
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ float4 s_buf[8][32];
+  __shared__ float4 s_grp[8][64];        // per warp: staged records (the cell's, or a batch of candidates)
   __shared__ float s_hits[8][512 + 32];  // per warp: one half-batch's in-range d2 + a trash row
   __shared__ uint32_t s_rsrc[8][kSoftRuns], s_rpre[8][kSoftRuns + 1];
   // 32-bit counts per CTA; a warp whose item could push the CTA past 2^31 (weighted) pairs writes
@@ -354,7 +440,11 @@ __global__ void __launch_bounds__(256) k_soft_fwd(const SoftArgs a) {
     old = __shfl_sync(0xffffffffu, old, 0);
     glob = old + inc >= (1ull << 31);
   };
-  soft_items_listed<SYM>(a, reinterpret_cast<float*>(s_buf[w]), s_rsrc[w], s_rpre[w], s_hits[w], pair, bound);
+  if (SYM)
+    soft_cells_sym(a, reinterpret_cast<float*>(s_grp[w]), s_rsrc[w], s_rpre[w], reinterpret_cast<uint32_t*>(s_hits[w]),
+                   pair, bound);
+  else
+    soft_items_listed(a, reinterpret_cast<float*>(s_grp[w]), s_rsrc[w], s_rpre[w], s_hits[w], pair, bound);
   __syncthreads();
   for (uint32_t m = threadIdx.x; m < nf; m += blockDim.x) {
     if (sM0[m]) {
@@ -625,8 +715,11 @@ int soft_forward(ps_grid* g, const float* dsrf, const uint64_t ctr_mask[4], floa
     // unordered pairs of neighbour records, weighted by the central flags of both ends
     rc = launch_grid_for(g, (const void*)k_soft_fwd<true>, smem, &blocks);
     if (rc) return rc;
-    rc = nbr_items(g, sa, s, PS_KID_SOFT_FWD);
-    if (rc) return rc;
+    // cells taken from the neighbour list's counter (owners = candidates = neighbour records)
+    PS_LAUNCH(PS_KID_SOFT_FWD, s, PS_CUDA(launch_pdl(k_reset_items, 1, 32, 0, s, g->nbr.geo)));
+    sa.orec = g->nbr.rec;
+    sa.ostart = g->nbr.start;
+    sa.ogeo = g->nbr.geo;
     sa.pfx = reinterpret_cast<const uint32_t*>(g->cr);
     PS_LAUNCH(PS_KID_SOFT_FWD, s, PS_CUDA(launch_pdl(k_soft_fwd<true>, blocks, 256, smem, s, sa)));
   } else {
