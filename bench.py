@@ -110,13 +110,19 @@ FLOPS_PER_CANDIDATE = 9
 
 
 def query_sources_sha256() -> str:
-    """Digest of the query kernels' sources: a stored ncu traffic figure holds only for this source."""
+    """Digest of the query kernels' sources (code lines only: // comments and blank lines are
+    left out, so that a comment edit keeps a record): a stored ncu traffic figure holds only for
+    this code."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in ("ps_query.cu", "ps_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2004_05188_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2004_05188_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = re.sub(r"//.*$", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

@@ -5,7 +5,8 @@
 // are merged afterwards (Suppl. "Customized user defined batch processing
 // queues").  Here the ROIs of one cell of the grid share their candidates: the
 // cells within `stencil` cells of it (27 cells for cells of edge >= r_cut, 125
-// for cells of edge >= r_cut/2), read as x-contiguous runs of sorted records.
+// for cells of edge >= r_cut/2, up to 343 for r_cut/3, less the cells that
+// cannot hold a pair within r_cut), read as x-contiguous runs of sorted records.
 // Two persistent kernels take work from device counters (the dynamic
 // schedule):
 //
@@ -24,6 +25,12 @@
 // Each thread keeps the k smallest squared distances in registers (sorted
 // insertion).  Counts go to per-CTA shared-memory histograms (the per-thread
 // buffers) added to the uint64 global histograms when the CTA finishes.
+//
+// The query in passes (ps_grid_opts.split) reuses the warp kernel for its near
+// kNN pass (vertex mode: the centrals sorted by the vertex-centred grid, each
+// item against the 2 x 2 x 2 cells around its vertex) and adds k_knn_list (the
+// full-radius kNN of the centrals that pass lists) and k_rdf_sym (the RDF over
+// unordered pairs of neighbour records).
 #include <cstring>
 #include <vector>
 
@@ -1328,7 +1335,8 @@ static void choose_lut(ps_bins bins, QueryArgs& qa) {
 // Two points whose cells are |d| >= 2 apart along an axis are more than (|d| - 1) r_cut cs apart
 // along it, so cell offset (dx, dy, dz) can hold a pair within r_cut only if
 // sum_i max(0, |d_i| - 1)^2 (cs (1 + 2^-10))^2 < 1; the test keeps a further 2^-20 margin.
-// Only stencils of three cells (cs < 1/2) lose cells: their 8 x 3 far corners of each octant.
+// Stencils of three cells (cs < 1/2) lose the 4 far corner cells of each octant; two-cell stencils
+// lose corners or rows only for cs above ~0.58.
 static void row_widths(int s, double cs, int8_t* w) {
   const int W = 2 * s + 1;
   const double f = cs * (1.0 + 1.0 / 1024.0), lim = (1.0 + 1.0 / 1048576.0) * (1.0 + 1.0 / 1048576.0);
