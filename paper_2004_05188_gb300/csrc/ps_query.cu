@@ -555,6 +555,8 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
           uint32_t nh = 0;  // hits in the warp list (uniform)
           uint32_t qn = 0;  // entries in this lane's queue column
           const float thr = top[KK - 1];
+          // vertex mode: no in-range count, one bound for the queue (the reach and the k-th distance)
+          const float thr_e = fminf(thr, emax);
 #pragma unroll 2
           for (uint32_t u = 0; u < n_it; ++u) {
             const uint32_t t = 8 * half + u * L + sub;
@@ -564,6 +566,15 @@ __global__ void __launch_bounds__(256) k_query_warp(const QueryArgs a) {
             dist2_x2(px, py, pz, xy.x, xy.y, zw.x, d2a, d2b);
             float wa, wb;
             f2_unpack(zw.y, wa, wb);
+            if constexpr (VX) {
+              const bool qa = d2a < thr_e && __float_as_uint(wa) != pidx;
+              const bool qb = d2b < thr_e && __float_as_uint(wb) != pidx;
+              kq[qn * 32 + lane] = d2a;
+              qn += (uint32_t)qa;
+              kq[qn * 32 + lane] = d2b;
+              qn += (uint32_t)qb;
+              continue;
+            }
             const bool ha = d2a < emax && __float_as_uint(wa) != pidx;
             const bool hb = d2b < emax && __float_as_uint(wb) != pidx;
             within += (uint32_t)ha + (uint32_t)hb;
