@@ -417,9 +417,9 @@ typedef enum {
   PS_KID_SELECT = 2,     /* neighbour-set selection + bounding box */
   PS_KID_GEOMETRY = 3,   /* cell geometry + zeroing of the counts */
   PS_KID_COUNT = 4,      /* cell index + rank of the neighbours */
-  PS_KID_SCAN = 5,       /* exclusive scan of cell counts (3 launches) */
-  PS_KID_SCATTER = 6,    /* counting-sort scatter */
-  PS_KID_CENTRAL = 7,    /* central reset + selection + cell rank */
+  PS_KID_SCAN = 5,       /* exclusive scans of cell counts and the central lists' cell starts */
+  PS_KID_SCATTER = 6,    /* counting-sort scatters (neighbours; vertex-centred centrals) */
+  PS_KID_CENTRAL = 7,    /* central reset + selection + cell rank (and the vertex-centred count) */
   PS_KID_QUERY = 8,      /* exact kNN + RDF query (the split query's near-radius kNN pass) */
   PS_KID_EPILOGUE = 9,   /* meta epilogue */
   PS_KID_SOFT_FWD = 10,  /* smoothed RDF forward */
