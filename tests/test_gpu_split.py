@@ -62,6 +62,16 @@ def test_cylinder_200k_split_full_size(ps, orc, spec):
     assert_same(g, r, [1, 10], per_central=True)
 
 
+def test_cylinder_200k_benchmark_configuration(ps, orc, spec):
+    """The 2e5 cylinder as the benchmark runs it (all-all, k = 1, r = [0, 0.01, 2] nm, d_srf >= 1
+    nm) in the configuration its autotuner picks there: third-size cells, the query in passes."""
+    xyz, t, d = spec.cylinder_small()
+    bins = ps.bins_from_spec(0.0, 0.01, 2.0)
+    r = orc.spatstat(xyz, t, d, "all", "all", 1.0, *bins, [1], per_central=True)
+    g = run_gpu(ps, xyz, t, d, "all", "all", 1.0, bins, [1], per_central="kth", cell_scale=1 / 3, split=True)
+    assert_same(g, r, [1], per_central="kth")
+
+
 @pytest.mark.parametrize("cell_scale", [0.5, 1 / 3])
 def test_needle_8m_sparse_types_split(ps, orc, spec, cell_scale):
     """Sc-Sc: almost no Sc has 5 Sc neighbours within 1 nm (0.67 nm with third-size cells), so
