@@ -1,0 +1,63 @@
+"""Host check of the near kNN pass's geometric guarantee (the query in passes on half-size cells):
+every record outside the 2 x 2 x 2 cells around a central's vertex lies at a squared distance of
+at least the central's reach.  The cell coordinates, the vertex-centred cells and the reach are
+restated here with float32 numpy arithmetic in the kernel's operation order (cell coordinate
+u = (x - origin) * inv_h; vertex cell from the origin half a cell lower; reach = (distance to the
+block's faces - slack) * h * (1 - 2^-12), squared, times (1 - 2^-12)), and checked by brute force
+on random clouds with points placed on and next to the cell faces."""
+import numpy as np
+import pytest
+
+f32 = np.float32
+
+
+def _grid(xyz, r_cut, cell_scale):
+    lo = xyz.min(axis=0).astype(np.float64)
+    hi = xyz.max(axis=0).astype(np.float64)
+    ext = float((hi - lo).max())
+    h = r_cut * cell_scale * (1.0 + 1.0 / 1024.0) + ext / 1048576.0
+    dims = np.floor((hi - lo) / h).astype(np.int64) + 1
+    org = lo.astype(np.float32)
+    hf = f32(h)
+    inv_h = f32(1.0 / h)
+    return org, hf, inv_h, dims
+
+
+def _cells(P, org, inv_h, dims):
+    u = (P - org).astype(f32) * inv_h  # two float32 roundings, as the kernel
+    c = np.floor(u).astype(np.int64)
+    return np.clip(c, 0, dims - 1), u
+
+
+@pytest.mark.parametrize("seed,n,box", [(1, 3000, 9.0), (2, 2500, 14.0), (3, 2000, 6.0)])
+def test_vertex_reach_bounds_every_record_outside_the_block(seed, n, box):
+    rng = np.random.default_rng(seed)
+    r_cut, cs = 2.0, 0.5
+    xyz = (rng.random((n, 3)) * box).astype(f32)
+    org, hf, inv_h, dims = _grid(xyz, r_cut, cs)
+    # points on, just below and just above the cell faces and the midplanes (the vertex cell's
+    # faces), where the rounding of the coordinates decides the cells
+    k = rng.integers(0, dims.min(), size=(n // 2, 3))
+    frac = rng.choice([0.0, 0.5, 1.0], size=(n // 2, 3))
+    eps = rng.choice([-1, 0, 1], size=(n // 2, 3)) * 2.0 ** -22 * box
+    face = (org.astype(np.float64) + (k + frac) / np.float64(inv_h) + eps).astype(f32)
+    xyz = np.concatenate([xyz, face])
+    org, hf, inv_h, dims = _grid(xyz, r_cut, cs)
+    c, u = _cells(xyz, org, inv_h, dims)
+    # vertex-centred cells: origin half a cell lower, one more cell per axis
+    org_v = (org - f32(f32(0.5) * hf)).astype(f32)
+    V, _ = _cells(xyz, org_v, inv_h, dims + 1)
+    # reach (kernel order)
+    slack = f32(float(dims.max()) * 5.0e-7 + 1.0e-6)
+    h_eff = f32(f32(1.0) / inv_h) * f32(1.0 - 1.0 / 4096.0)
+    m = np.minimum(u - (V.astype(f32) - f32(1.0)), (V.astype(f32) + f32(1.0)) - u).astype(f32).min(axis=1)
+    r = (np.maximum(m - slack, f32(0.0)) * h_eff).astype(f32)
+    e = ((r * r).astype(f32) * f32(1.0 - 1.0 / 4096.0)).astype(f32)
+    assert np.all(m > 0.45)  # every central is about half a cell or more inside its block
+    # brute force: records outside the block [V - 1, V] (neighbour-cell coordinates) per axis
+    for i in range(xyz.shape[0]):
+        outside = np.any((c < V[i] - 1) | (c > V[i]), axis=1)
+        q = xyz[outside]
+        dx, dy, dz = (q[:, 0] - xyz[i, 0]), (q[:, 1] - xyz[i, 1]), (q[:, 2] - xyz[i, 2])
+        d2 = ((dx * dx + dy * dy).astype(f32) + (dz * dz)).astype(f32)
+        assert d2.size == 0 or d2.min() >= e[i], (i, float(d2.min()), float(e[i]))
