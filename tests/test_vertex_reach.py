@@ -61,3 +61,33 @@ def test_vertex_reach_bounds_every_record_outside_the_block(seed, n, box):
         dx, dy, dz = (q[:, 0] - xyz[i, 0]), (q[:, 1] - xyz[i, 1]), (q[:, 2] - xyz[i, 2])
         d2 = ((dx * dx + dy * dy).astype(f32) + (dz * dz)).astype(f32)
         assert d2.size == 0 or d2.min() >= e[i], (i, float(d2.min()), float(e[i]))
+
+
+@pytest.mark.parametrize("cell_scale", [1 / 3, 0.4, 0.75, 0.6])
+def test_skipped_cells_hold_no_pair_within_r_cut(cell_scale):
+    """The stencil rows' widths (the cells a query skips because their gap to the central cell is
+    at least r_cut on the cell-edge bound): every pair with float32 d2 below r_cut^2 lies in a
+    kept cell offset, by brute force over a dense random cloud with points on the cell faces."""
+    import bench
+
+    rng = np.random.default_rng(11)
+    r_cut = 2.0
+    xyz = (rng.random((2500, 3)) * 7.0).astype(f32)
+    org, hf, inv_h, dims = _grid(xyz, r_cut, cell_scale)
+    k = rng.integers(0, dims.min(), size=(1500, 3))
+    face = (org.astype(np.float64) + k / np.float64(inv_h)
+            + rng.choice([-1, 0, 1], size=(1500, 3)) * 2.0 ** -22 * 7.0).astype(f32)
+    xyz = np.concatenate([xyz, face])
+    org, hf, inv_h, dims = _grid(xyz, r_cut, cell_scale)
+    c, _ = _cells(xyz, org, inv_h, dims)
+    s = 1 if cell_scale >= 1.0 else (2 if cell_scale >= 0.5 else 3)
+    w = np.array(bench.row_widths(s, cell_scale))  # [dz + s][dy + s]
+    E = f32(r_cut * r_cut)
+    for i in range(xyz.shape[0]):
+        dx, dy, dz = (xyz[:, 0] - xyz[i, 0]), (xyz[:, 1] - xyz[i, 1]), (xyz[:, 2] - xyz[i, 2])
+        d2 = ((dx * dx + dy * dy).astype(f32) + (dz * dz)).astype(f32)
+        near = d2 < E
+        off = c[near] - c[i]
+        assert np.all(np.abs(off) <= s), i
+        width = w[off[:, 2] + s, off[:, 1] + s]
+        assert np.all(np.abs(off[:, 0]) <= width), (i, off[np.abs(off[:, 0]) > width][:3])
