@@ -91,3 +91,30 @@ def test_skipped_cells_hold_no_pair_within_r_cut(cell_scale):
         assert np.all(np.abs(off) <= s), i
         width = w[off[:, 2] + s, off[:, 1] + s]
         assert np.all(np.abs(off[:, 0]) <= width), (i, off[np.abs(off[:, 0]) > width][:3])
+
+
+def test_first_tier_reach_of_the_full_radius_pass():
+    """The full-radius pass settles a central after the 27 cells around its cell when its k-th
+    distance lies within its reach to the faces of that block (cells c - 1 .. c + 1): no record
+    outside those cells lies below the reach."""
+    rng = np.random.default_rng(5)
+    r_cut, cs = 2.0, 0.5
+    xyz = (rng.random((2500, 3)) * 10.0).astype(f32)
+    org, hf, inv_h, dims = _grid(xyz, r_cut, cs)
+    k = rng.integers(0, dims.min(), size=(1500, 3))
+    face = (org.astype(np.float64) + k / np.float64(inv_h)
+            + rng.choice([-1, 0, 1], size=(1500, 3)) * 2.0 ** -22 * 10.0).astype(f32)
+    xyz = np.concatenate([xyz, face])
+    org, hf, inv_h, dims = _grid(xyz, r_cut, cs)
+    c, u = _cells(xyz, org, inv_h, dims)
+    slack = f32(float(dims.max()) * 5.0e-7 + 1.0e-6)
+    h_eff = f32(f32(1.0) / inv_h) * f32(1.0 - 1.0 / 4096.0)
+    m = np.minimum(u - (c.astype(f32) - f32(1.0)), (c.astype(f32) + f32(2.0)) - u).astype(f32).min(axis=1)
+    r = (np.maximum(m - slack, f32(0.0)) * h_eff).astype(f32)
+    e = ((r * r).astype(f32) * f32(1.0 - 1.0 / 4096.0)).astype(f32)
+    for i in range(xyz.shape[0]):
+        outside = np.any(np.abs(c - c[i]) > 1, axis=1)
+        q = xyz[outside]
+        dx, dy, dz = (q[:, 0] - xyz[i, 0]), (q[:, 1] - xyz[i, 1]), (q[:, 2] - xyz[i, 2])
+        d2 = ((dx * dx + dy * dy).astype(f32) + (dz * dz)).astype(f32)
+        assert d2.size == 0 or d2.min() >= e[i], (i, float(d2.min()), float(e[i]))
