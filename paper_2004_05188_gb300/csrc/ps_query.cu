@@ -410,11 +410,12 @@ __device__ __forceinline__ void vertex_run(const QueryArgs& a, const Geo& ng, co
 }
 
 // The squared reach of central p in vertex cell c: the distance from p to the nearest face of
-// the block (cells V - 1 .. V + 1 in the neighbour grid's cell coordinate u = (x - origin) *
-// inv_h), less a slack for the float32 rounding of the cell coordinates of p and of any record
-// (a few ulps of u, below slack cells), times the cell edge, shrunk by 2^-12 before and after
-// squaring: every record outside the block has d2 above it, so a k-th distance below it is the
-// k-th distance over the whole cloud.  Capped at E[nb].
+// its block (cells V - 1 and V along each axis, faces at u = V - 1 and u = V + 1 in the
+// neighbour grid's cell coordinate u = (x - origin) * inv_h), less a slack for the float32
+// rounding of the cell coordinates of p and of any record (a few ulps of u, below slack cells),
+// times the cell edge, shrunk by 2^-12 before and after squaring: every record outside the
+// block has d2 above it, so a k-th distance below it is the k-th distance over the whole cloud.
+// Capped at E[nb].
 __device__ __forceinline__ float vertex_reach(const Geo& ng, const Geo& vg, uint32_t c, const float4& p, float slack,
                                               float h_eff, float Emax) {
   const uint32_t v[3] = {c % vg.dims[0], (c / vg.dims[0]) % vg.dims[1], c / (vg.dims[0] * vg.dims[1])};
